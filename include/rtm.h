@@ -1,0 +1,197 @@
+/*
+ * rtm.h — C ABI of the GB300 reverse-time-migration (RTM) library.
+ *
+ * The library computes the data-parallel stage of the uncertainty-quantified
+ * seismic imaging workflow of "A workflow for seismic imaging with quantified
+ * uncertainty" (arXiv 2001.06444): for every velocity sample of an ensemble and
+ * every shot, 2D constant-density acoustic modelling (§2.2, Eq. 4, discretised
+ * 2nd order in time and 8th order in space as stated in §3), reverse-time
+ * propagation of the recorded data (§3, the adjoint problem), the
+ * source-normalised zero-lag cross-correlation imaging condition (§2.2, Eq. 5),
+ * shot stacking and the Laplacian filter on the brute stack (§3), and per-pixel
+ * ensemble statistics of the images (§2.3).
+ *
+ * Discrete definition (the paper leaves these unstated; one reading is fixed):
+ *   padded grid NZ x NX = (nz + 2 nb) x (nx + 2 nb), sponge of nb cells on all
+ *   four sides outside the physical grid, velocity edge-replicated into it;
+ *   c = (v dt)^2;  L = 8th-order central Laplacian with coefficients
+ *   {-205/72, 8/5, -1/5, 8/315, -1/560} / h^2 per axis, zero beyond the padded
+ *   grid;  sponge g = g_x g_z, g_1(k) = exp(-(0.015 (nb - k))^2) at distance k
+ *   from the outer edge (k < nb), 1 inside;  h = sqrt(g);
+ *   u^{n+1} = h (2 h u^n + c L(h u^n)) - g^2 u^{n-1} + c f^n,
+ *   f^n = wavelet[n] / (dx dz) at the source cell, u^0 = u^{-1} = 0,
+ *   trace sample d[n][r] = u^{n+1}(receiver r), n = 0 .. nt-1.
+ *   Backward (exact discrete adjoint, the same recurrence):
+ *   w^k = h (2 h w^{k+1} + c L(h w^{k+1})) - g^2 w^{k+2} + c R^T d[k-1],
+ *   k = nt .. 1, w^{nt+1} = w^{nt+2} = 0.
+ *   Imaging set K = { k : 1 <= k <= nt, k mod isnap == 0 }:
+ *   num = sum_K S^k w^k, den = sum_K (S^k)^2 with S^k = u^k (optionally
+ *   quantised), I_shot = num / (den + eps max(den)), stack = sum over shots,
+ *   optional filter I_f = -(D_zz + D_xx) I_stack (3-point, replicated edges).
+ *
+ * Conventions for every call:
+ *   - Arrays are row-major, x fastest: velocity / image [nz][nx],
+ *     seismograms [shot][nt][nrec].
+ *   - Large arrays (velocity, seismograms, images, statistics) may be device
+ *     memory or host memory; host buffers are staged through device memory on
+ *     the given stream and the call then synchronises that stream.  Device
+ *     buffers are used in place, the call is asynchronous on `stream` (a
+ *     cudaStream_t, NULL = the legacy default stream) unless stated otherwise.
+ *   - Acquisition arrays (source and receiver indices, the wavelet) are small
+ *     and are always HOST memory; they are copied during the call.
+ *   - The caller owns every pointer it passes.  The library owns its work
+ *     buffers (wavefields, snapshot store, partial images), which live in a
+ *     stream-ordered pool of the context and are reused across calls.
+ *   - Every call returns an rtm_status; no call aborts the process.  After an
+ *     error, rtm_last_error(ctx) describes it.
+ *   - One context serves one device and may be used from one host thread at a
+ *     time (the request loop has its own worker thread inside).
+ */
+#ifndef RTM_H
+#define RTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RTM_OK = 0,
+  RTM_ERR_ARG = 1,     /* bad shape, null pointer, index outside the physical grid */
+  RTM_ERR_CFL = 2,     /* the velocity violates the leapfrog stability bound       */
+  RTM_ERR_NOMEM = 3,   /* the work can never fit the context's memory budget       */
+  RTM_ERR_BUSY = 4,    /* request queue full                                        */
+  RTM_ERR_TIMEOUT = 5, /* a bounded wait expired                                    */
+  RTM_ERR_CUDA = 6,    /* a CUDA runtime call failed                                */
+  RTM_ERR_STATE = 7    /* unknown ticket or context state                           */
+} rtm_status;
+
+enum { RTM_SNAP_F32 = 0, RTM_SNAP_BF16 = 1, RTM_SNAP_F16 = 2 };
+
+enum { RTM_REQ_QUEUED = 0, RTM_REQ_RUNNING = 1, RTM_REQ_DONE = 2, RTM_REQ_FAILED = 3 };
+
+typedef struct rtm_ctx rtm_ctx;
+
+/* Grid of one migration (§4.1 describes the experiments by extent and
+ * velocities; spacing and step count are the caller's).  nx, nz: physical
+ * cells; nb: sponge width added on every side; dx, dz in m; dt in s;
+ * nt: number of time updates. */
+typedef struct {
+  int nx, nz, nb;
+  double dx, dz, dt;
+  int nt;
+} rtm_grid;
+
+/* Acquisition (Listing 1 of §4.3 loops over shot locations; §4.1/§4.2 record
+ * with near-surface hydrophones).  Indices are PHYSICAL grid cells:
+ * 0 <= ix < nx, 0 <= iz < nz.  All pointers are host memory.  One receiver
+ * spread and one wavelet (nt samples, wavelet[n] = w(n dt)) serve all shots. */
+typedef struct {
+  int nshot;
+  const int *src_ix, *src_iz;   /* [nshot] */
+  int nrec;
+  const int *rec_ix, *rec_iz;   /* [nrec] */
+  const float *wavelet;         /* [nt] */
+} rtm_acq;
+
+/* Migration options.  isnap: imaging interval (>= 1); snap_dtype: RTM_SNAP_*,
+ * storage of the forward snapshots S^k (F16: q = RN(S/s), s = max|S^k| / 2^15;
+ * BF16: s = max|S^k|; F32: exact); eps: stabiliser of the source
+ * normalisation of Eq. 5 (typical 1e-6); laplacian: 1 applies the §3 filter. */
+typedef struct {
+  int isnap;
+  int snap_dtype;
+  double eps;
+  int laplacian;
+} rtm_opts;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the context may hold for work buffers (0 = 85% of the free
+ * memory at creation).  Returns RTM_ERR_ARG for a null ctx pointer or a bad
+ * device, RTM_ERR_CUDA if the device cannot be initialised. */
+int rtm_ctx_create(rtm_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context: waits (bounded) for in-flight requests, frees every
+ * buffer it owns.  NULL is accepted. */
+int rtm_ctx_destroy(rtm_ctx *ctx);
+
+/* Forward modelling of one shot (§2.2, Eq. 4 with the wavelet as source term;
+ * Listing 1, `isotropicAcousticModeling`).  vel: [nz][nx] m/s; shot: index
+ * into acq; seis: [nt][nrec] output, d[n][r] = u^{n+1}(receiver r).
+ * Checks the CFL bound of §3 (RTM_ERR_CFL) before any launch. */
+int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
+              const rtm_acq *acq, int shot, float *seis, void *stream);
+
+/* Reverse time migration of all shots of acq over one velocity model
+ * (§2.2 Eq. 5 imaging, §3 Laplacian on the brute stack; Listing 1 loop).
+ * seis: [nshot][nt][nrec] observed data; image: [nz][nx] output (the filtered
+ * stack if opts->laplacian, else the plain stack).  Shots are processed in
+ * batches sized to the memory budget; the stack is Kahan-compensated FP32 in
+ * shot order, so the result does not depend on the batch size. */
+int rtm_migrate(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
+                const rtm_acq *acq, const float *seis, const rtm_opts *opts,
+                float *image, void *stream);
+
+/* Migration of the same shots over an ensemble of nsample velocity models
+ * (the Monte Carlo loop of §2 / §3 stage 2).  vels: [nsample][nz][nx];
+ * images: [nsample][nz][nx].  All (sample, shot) migrations are scheduled as
+ * independent work items; images[s] equals rtm_migrate of vels[s]. */
+int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample,
+                         const float *vels, const rtm_acq *acq,
+                         const float *seis, const rtm_opts *opts,
+                         float *images, void *stream);
+
+/* Per-pixel statistics of n images (§2.3; stage 3 of §3): mean and standard
+ * deviation (divisor n-1; 0 when n == 1) reduced in FP64, and the 5% and 95%
+ * quantiles (linear interpolation between order statistics at h = (n-1) p).
+ * images: [n][npix] float; mean, std: [npix] double; q05, q95: [npix] float. */
+int rtm_ensemble_stats(rtm_ctx *ctx, const float *images, int n, long npix,
+                       double *mean, double *std_, float *q05, float *q95,
+                       void *stream);
+
+/* Uncertainty maps of Eqs. 6 and 7 (§2.3) from a standard-deviation map and
+ * a mean map: c = (s_max - s) / (s_max - s_min) (1 where s_max == s_min) and
+ * r = s / mean (0 where mean == 0).  All arrays [npix] double. */
+int rtm_uncertainty_maps(rtm_ctx *ctx, const double *mean, const double *std_,
+                         long npix, double *conf, double *ratio, void *stream);
+
+/* A migration request for the request loop (continuous batching).  All
+ * pointers must stay valid until rtm_poll reports DONE or FAILED; vel, seis
+ * and image are device memory. */
+typedef struct {
+  rtm_grid grid;
+  const float *vel;
+  rtm_acq acq;
+  const float *seis;
+  rtm_opts opts;
+  float *image;
+} rtm_request;
+
+/* Queue a migration request; its shots join the device work of requests
+ * already in flight as soon as memory for their snapshot buffers is free.
+ * Returns RTM_ERR_NOMEM if the request could never fit the budget,
+ * RTM_ERR_BUSY if the queue is full, RTM_ERR_CFL / RTM_ERR_ARG as rtm_migrate. */
+int rtm_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket);
+
+/* State of a request (RTM_REQ_*), waiting up to timeout_ms for it to reach
+ * DONE or FAILED (0 = do not wait).  Returns RTM_ERR_TIMEOUT if the wait
+ * expired first (the state is still written), RTM_ERR_STATE for an unknown
+ * ticket.  A DONE or FAILED ticket is forgotten after it is reported. */
+int rtm_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms);
+
+/* Text of the last error on this context (never NULL). */
+const char *rtm_last_error(rtm_ctx *ctx);
+
+/* The largest v dt / min(dx, dz) the scheme is stable for: 2 / sqrt(2 * 2048/315)
+ * for square cells (§3: every RTM checks its own CFL condition).  For
+ * rectangular cells the bound the library applies is
+ * v dt sqrt((1/dx^2 + 1/dz^2) 2048/315) <= 2. */
+double rtm_cfl_limit(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTM_H */

@@ -1,0 +1,138 @@
+"""Pins of the oracle's propagation and imaging against what mathematics and
+the paper fix, independent of the oracle's own formulas:
+
+- homogeneous-medium traces against the analytic 2D Green's function of
+  Eq. 4 convolved with the Ricker wavelet (scaling of the source term and the
+  time origin of the traces);
+- dot test: reverse-time propagation is the transpose of modelling (§3, the
+  adjoint problem), to FP64 rounding;
+- dot test: the raw imaging numerator of Eq. 5 is the transpose of Born
+  modelling with the stored source wavefield;
+- source-receiver reciprocity of the symmetric scheme;
+- the flat reflector of the two-layer model is imaged at its depth with the
+  sign of the reflection coefficient (§2.2: the normalised image has the sign
+  of the reflection coefficient).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_l2
+from paper_2001_06444_gb300 import inputs
+
+
+def _green_ricker(r, v, f, t):
+    """(1/2pi) int_0^{acosh(vt/r)} w(t - (r/v) cosh th) dth for each t."""
+    out = np.zeros_like(t)
+    t0 = 1.0 / f
+    for n, tn in enumerate(t):
+        if v * tn <= r:
+            continue
+        top = math.acosh(v * tn / r)
+        th = np.linspace(0.0, top, 20001)
+        tau = tn - (r / v) * np.cosh(th)
+        a = (np.pi * f * (tau - t0)) ** 2
+        w = (1.0 - 2.0 * a) * np.exp(-a)
+        out[n] = np.trapezoid(w, th) / (2.0 * np.pi)
+    return out
+
+
+def test_homogeneous_traces_match_analytic_green_function():
+    v, d, dt, f, nt = 2000.0, 5.0, 4e-4, 15.0, 1000
+    n = 321
+    g = oracle.grid(n, n, 20, d, d, dt, nt)
+    vel = np.full((n, n), v)
+    c = n // 2
+    offsets = np.array([40, 60, 80, 100])  # 200 .. 500 m
+    rx = (c + offsets).astype(np.int32)
+    rz = np.full(offsets.size, c, np.int32)
+    w = inputs.ricker(f, dt, nt)
+    seis = oracle.model(g, vel, c, c, rx, rz, w)
+    t = (np.arange(nt) + 1) * dt  # sample n is time (n + 1) dt
+    errs = []
+    for k, off in enumerate(offsets):
+        ana = _green_ricker(off * d, v, f, t)
+        errs.append(rel_l2(seis[:, k], ana))
+    # measured 0.10-0.24% (dispersion of the 2nd-order time stepping); a missing
+    # c or 1/(dx dz) factor, or a one-sample shift of the time origin (3.6-4.0%),
+    # exceeds 1%
+    assert max(errs) < 1e-2, errs
+
+
+def _random_problem(seed, nz=26, nx=31, nb=6, nt=160):
+    u = inputs.uniform(seed, nz * nx).reshape(nz, nx)
+    vel = 1500.0 + 1500.0 * u
+    g = oracle.grid(nx, nz, nb, 10.0, 8.0, 1.2e-3, nt)
+    assert oracle.courant(vel.max(), g.dt, g.dx, g.dz) < 1.0
+    rx = np.array([2, 7, 13, 21, 29, 7], np.int32)
+    rz = np.array([1, 3, 0, 20, 25, 3], np.int32)  # includes a duplicate cell
+    return g, vel, rx, rz
+
+
+def test_dot_test_modelling_vs_reverse_propagation():
+    g, vel, rx, rz = _random_problem(11)
+    f = inputs.normal(12, g.nt)
+    dobs = inputs.normal(13, g.nt * rx.size).reshape(g.nt, rx.size)
+    Ff = oracle.model(g, vel, 17, 9, rx, rz, f)
+    Ftd = oracle.adjoint_at_source(g, vel, 17, 9, rx, rz, dobs)
+    lhs = float(np.sum(Ff * dobs))
+    rhs = float(np.sum(f * Ftd))
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), abs(rhs))
+
+
+@pytest.mark.parametrize("isnap", [1, 3])
+def test_dot_test_born_vs_imaging_numerator(isnap):
+    g, vel, rx, rz = _random_problem(21, nt=140)
+    w = inputs.ricker(25.0, g.dt, g.nt)
+    m = inputs.normal(22, g.nz * g.nx).reshape(g.nz, g.nx)
+    dobs = inputs.normal(23, g.nt * rx.size).reshape(g.nt, rx.size)
+    Bm = oracle.born(g, vel, 17, 9, rx, rz, w, isnap, m)
+    _, num, _ = oracle.migrate(g, vel, [17], [9], rx, rz, w, dobs[None], isnap=isnap,
+                               laplacian=False, return_parts=True)
+    lhs = float(np.sum(Bm * dobs))
+    rhs = float(np.sum(m * num[0]))
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), abs(rhs))
+
+
+def test_reciprocity():
+    g, vel, _, _ = _random_problem(31)
+    w = inputs.ricker(20.0, g.dt, g.nt)
+    a = (4, 3)   # (ix, iz)
+    b = (25, 19)
+    dab = oracle.model(g, vel, a[0], a[1], [b[0]], [b[1]], w)[:, 0]
+    dba = oracle.model(g, vel, b[0], b[1], [a[0]], [a[1]], w)[:, 0]
+    assert rel_l2(dab, dba) < 1e-10
+
+
+def _reflector_profile(data, s, g, vmig):
+    img = oracle.migrate(g, vmig, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet,
+                         data[None], isnap=1, laplacian=True)
+    return img[:, 50:151].mean(axis=1)  # x in [500, 1500] m
+
+
+def test_flat_reflector_depth_and_sign():
+    """Two-layer model (1500 / 2500 m/s, step between z = 490 and 500 m),
+    direct wave removed, migrated with the background velocity above the
+    reflector.  Zero-lag cross-correlation of a 2D point-source survey rotates
+    the image wavelet by about -90 degrees, so (a) the envelope of the depth
+    profile locates the reflector and (b) after the matching -d/dt filter on
+    the data the image peaks at the reflector with the sign of R = +0.25."""
+    from scipy.signal import hilbert
+
+    s = inputs.flat_reflector()
+    g = oracle.grid(*s.grid_tuple())
+    d_two = oracle.model(g, s.vel, s.src_ix[0], s.src_iz[0], s.rec_ix, s.rec_iz, s.wavelet)
+    v0 = np.full_like(s.vel, 1500.0)
+    d_dir = oracle.model(g, v0, s.src_ix[0], s.src_iz[0], s.rec_ix, s.rec_iz, s.wavelet)
+    data = d_two - d_dir
+    iz0, iz1 = 10, 91  # z in [100, 900] m
+    prof = _reflector_profile(data, s, g, v0)
+    env = np.abs(hilbert(prof))
+    pick = iz0 + int(np.argmax(env[iz0:iz1]))
+    assert abs(pick * s.dz - 495.0) <= 10.0, pick
+    prof_zp = _reflector_profile(-np.gradient(data, axis=0), s, g, v0)
+    k = iz0 + int(np.argmax(np.abs(prof_zp[iz0:iz1])))
+    assert abs(k * s.dz - 495.0) <= 10.0, k
+    assert prof_zp[k] > 0
