@@ -117,10 +117,42 @@ int rtm_ctx_create(rtm_ctx **ctx, int device, size_t hbm_budget_bytes);
  * buffer it owns.  NULL is accepted. */
 int rtm_ctx_destroy(rtm_ctx *ctx);
 
-/* Forward modelling of one shot (§2.2, Eq. 4 with the wavelet as source term;
- * Listing 1, `isotropicAcousticModeling`).  vel: [nz][nx] m/s; shot: index
- * into acq; seis: [nt][nrec] output, d[n][r] = u^{n+1}(receiver r).
- * Checks the CFL bound of §3 (RTM_ERR_CFL) before any launch. */
+/* Cap the number of (sample, shot) migrations the context keeps in flight at
+ * once (0 = as many as the memory budget holds).  More items per launch hide
+ * latency; fewer keep the working set in L2.  Returns RTM_ERR_ARG if
+ * max_items < 0. */
+int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items);
+
+/* Counters of the propagation kernels, accumulated while profiling is on.
+ * step_ms is device time measured with CUDA events around each run of
+ * back-to-back step launches (forward or backward phase of a batch);
+ * step_bytes counts the algorithmic bytes of those launches: 16 B per padded
+ * point update (read u^n, u^{n-1}, c; write u^{n+1}), plus b per physical
+ * pixel for each snapshot stored or read (b = 4 or 2) and 16 B per physical
+ * pixel per imaging step (num and den read and written).  launches counts
+ * every kernel the library launched. */
+typedef struct {
+  long long step_launches;
+  double step_ms;
+  double step_bytes;
+  double point_updates;
+  long long launches;
+  long long migrations;
+} rtm_stats;
+
+/* Turn profiling on (1) or off (0).  With profiling on, every migration
+ * call synchronises its stream at the end to read its events. */
+int rtm_ctx_set_profiling(rtm_ctx *ctx, int on);
+
+/* Copy the counters into *out; reset them if reset != 0. */
+int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset);
+
+/* Forward modelling (§2.2, Eq. 4 with the wavelet as source term; Listing 1,
+ * `isotropicAcousticModeling`).  vel: [nz][nx] m/s; shot: index into acq, or
+ * -1 for every shot of acq (advanced side by side); seis: output
+ * [nt][nrec] for one shot, [nshot][nt][nrec] for all, with
+ * d[n][r] = u^{n+1}(receiver r).  Checks the CFL bound of §3 (RTM_ERR_CFL)
+ * before any launch. */
 int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
               const rtm_acq *acq, int shot, float *seis, void *stream);
 

@@ -77,6 +77,7 @@ def lib():
             L.oracle_courant.argtypes = [C.c_double] * 4
             L.oracle_courant.restype = C.c_double
             L.oracle_sponge.argtypes = [g, dp]
+            L.oracle_threads.restype = C.c_int
             _lib = L
     return _lib
 
@@ -202,3 +203,8 @@ def sponge(g: Grid):
     out = np.zeros((g.nz + 2 * g.nb, g.nx + 2 * g.nb), np.float64)
     lib().oracle_sponge(C.byref(g), out.ctypes.data_as(C.POINTER(C.c_double)))
     return out
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(lib().oracle_threads())

@@ -106,7 +106,8 @@ static void laplacian8(const double *a, int NZ, int NX, double dz, double dx,
 static void step(const or_model *m, const or_grid *gr, const double *ucur,
                  const double *uold, double *unew, double *hu, double *lap) {
   size_t n = (size_t)m->NZ * m->NX;
-  for (size_t p = 0; p < n; ++p) hu[p] = m->h[p] * ucur[p];
+#pragma omp parallel for schedule(static)
+  for (long p = 0; p < (long)n; ++p) hu[p] = m->h[p] * ucur[p];
   laplacian8(hu, m->NZ, m->NX, gr->dz, gr->dx, lap);
 #pragma omp parallel for schedule(static)
   for (long p = 0; p < (long)n; ++p)
@@ -389,6 +390,16 @@ double oracle_courant(double vmax, double dt, double dx, double dz) {
   for (int m = 0; m <= 4; ++m) sym += (m == 0 ? 1.0 : 2.0) * A8[m] * ((m % 2) ? -1.0 : 1.0);
   sym = -sym;
   return vmax * dt * sqrt((1.0 / (dx * dx) + 1.0 / (dz * dz)) * sym) / 2.0;
+}
+
+/* Number of threads the oracle's parallel loops use. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* The padded-grid sponge factor g, exposed for tests: [NZ][NX]. */

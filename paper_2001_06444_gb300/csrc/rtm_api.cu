@@ -1,0 +1,785 @@
+// rtm_api.cu — C ABI entry points and the migration engine (host side).
+//
+// The engine schedules (velocity sample, shot) migrations as independent work
+// items, B of them in flight at a time (B sized by the memory budget), each
+// launch of the step kernel advancing all B grids by one time step:
+//   forward   n = 0 .. nt-1: u^{n+1} from u^n, u^{n-1}; source c f^n;
+//             snapshot S^n stored when n is in K (scale reduced one launch
+//             earlier);
+//   backward  k = nt .. 1:   w^k from w^{k+1}, w^{k+2}; data c R^T d[k-1];
+//             imaging num += S^k w^k, den += (S^k)^2 when k is in K;
+//   per item: I = num / (den + eps max den), Kahan-added in shot order to
+//             its sample's stack;
+//   per call: Laplacian filter of each stack (§3).
+// This is Listing 1's shot loop (forward modelling, then adjoint modelling
+// with imaging) with the shots and the Monte Carlo samples of §3 run side by
+// side on one GPU instead of in MPI subgroups.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "rtm_engine.h"
+#include "rtm_launch.h"
+
+namespace rtm {
+
+int fail(rtm_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CU(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, RTM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+cudaError_t DevBuf::alloc(rtm_ctx *ctx, size_t n, cudaStream_t s) {
+  release();
+  st = s;
+  bytes = n;
+  if (n == 0) return cudaSuccess;
+  return cudaMallocFromPoolAsync(&p, n, ctx->pool, s);
+}
+
+void DevBuf::release() {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+  bytes = 0;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
+
+Geo make_geo(const rtm_grid &gr) {
+  Geo g;
+  g.nb = gr.nb;
+  g.nz = gr.nz;
+  g.nx = gr.nx;
+  g.NZ = gr.nz + 2 * gr.nb;
+  g.NX = gr.nx + 2 * gr.nb;
+  g.X0 = (4 - gr.nb % 4) % 4;
+  g.CP = g.X0 + gr.nb;
+  g.SX = (int)round_up(gr.nx, 4);
+  // the pitch covers the padded domain and the 4-aligned physical window
+  g.P = (int)round_up(std::max(g.X0 + g.NX, g.CP + g.SX), 32);
+  g.ntx = (g.P + TX - 1) / TX;
+  g.ntz = (g.NZ + TZ - 1) / TZ;
+  g.plane = (long long)g.NZ * g.P;
+  g.pplane = (long long)g.nz * g.SX;
+  return g;
+}
+
+// 8th-order central second-derivative weights (§3: eighth order in space).
+static const double kA8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+Coef make_coef(const rtm_grid &gr) {
+  Coef k;
+  const double rx = 1.0 / (gr.dx * gr.dx), rz = 1.0 / (gr.dz * gr.dz);
+  k.c0 = (float)(kA8[0] * (rx + rz));
+  for (int m = 1; m <= 4; ++m) {
+    k.ax[m - 1] = (float)(kA8[m] * rx);
+    k.az[m - 1] = (float)(kA8[m] * rz);
+  }
+  return k;
+}
+
+static size_t snap_elem_bytes(int dtype) { return dtype == RTM_SNAP_F32 ? 4 : 2; }
+
+MigrationPlan plan_migration(const rtm_grid &gr, const rtm_acq &acq, const rtm_opts &op,
+                             int nsample) {
+  MigrationPlan p;
+  p.g = make_geo(gr);
+  p.nsnap = gr.nt / op.isnap;
+  const Geo &g = p.g;
+  p.item_bytes = 2 * (size_t)g.plane * 4 + (size_t)p.nsnap * g.pplane * snap_elem_bytes(op.snap_dtype) +
+                 2 * (size_t)g.pplane * 4 + (size_t)(p.nsnap + 1) * 4 + 256 * 6;
+  p.shared_bytes = (size_t)nsample * g.plane * 4 + (size_t)g.P * 4 + (size_t)g.NZ * 4 +
+                   (size_t)acq.nshot * 8 + (size_t)(g.ntx * g.ntz + 1) * 4 +
+                   (size_t)acq.nrec * 8 + (size_t)gr.nt * 4 + 2 * (size_t)nsample * g.pplane * 4 +
+                   (size_t)acq.nshot * (size_t)nsample * 8 + 4096;
+  return p;
+}
+
+// -------------------------------------------------------------- checks --
+
+int check_grid(rtm_ctx *ctx, const rtm_grid *g) {
+  if (!g) return fail(ctx, RTM_ERR_ARG, "grid is NULL");
+  if (g->nx < 1 || g->nz < 1 || g->nb < 0 || g->nt < 1)
+    return fail(ctx, RTM_ERR_ARG, "bad grid sizes nx=%d nz=%d nb=%d nt=%d", g->nx, g->nz, g->nb,
+                g->nt);
+  if (!(g->dx > 0 && g->dz > 0 && g->dt > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dz) ||
+      !std::isfinite(g->dt))
+    return fail(ctx, RTM_ERR_ARG, "bad spacing dx=%g dz=%g dt=%g", g->dx, g->dz, g->dt);
+  const long long NZ = (long long)g->nz + 2LL * g->nb, NX = (long long)g->nx + 2LL * g->nb;
+  if (NZ * (NX + 64) >= (1LL << 31) || NZ > 65535LL * TZ)
+    return fail(ctx, RTM_ERR_ARG, "grid too large (%lld x %lld padded)", NZ, NX);
+  return RTM_OK;
+}
+
+int check_acq(rtm_ctx *ctx, const rtm_grid *g, const rtm_acq *a, bool need_rec) {
+  if (!a) return fail(ctx, RTM_ERR_ARG, "acquisition is NULL");
+  if (a->nshot < 1 || !a->src_ix || !a->src_iz)
+    return fail(ctx, RTM_ERR_ARG, "need at least one source (nshot=%d)", a->nshot);
+  if (a->nrec < (need_rec ? 1 : 0) || (a->nrec > 0 && (!a->rec_ix || !a->rec_iz)))
+    return fail(ctx, RTM_ERR_ARG, "bad receiver set (nrec=%d)", a->nrec);
+  if (!a->wavelet) return fail(ctx, RTM_ERR_ARG, "wavelet is NULL");
+  for (int s = 0; s < a->nshot; ++s)
+    if (a->src_ix[s] < 0 || a->src_ix[s] >= g->nx || a->src_iz[s] < 0 || a->src_iz[s] >= g->nz)
+      return fail(ctx, RTM_ERR_ARG, "source %d at (ix=%d, iz=%d) is outside the %dx%d grid", s,
+                  a->src_ix[s], a->src_iz[s], g->nx, g->nz);
+  for (int r = 0; r < a->nrec; ++r)
+    if (a->rec_ix[r] < 0 || a->rec_ix[r] >= g->nx || a->rec_iz[r] < 0 || a->rec_iz[r] >= g->nz)
+      return fail(ctx, RTM_ERR_ARG, "receiver %d at (ix=%d, iz=%d) is outside the %dx%d grid", r,
+                  a->rec_ix[r], a->rec_iz[r], g->nx, g->nz);
+  for (int n = 0; n < g->nt; ++n)
+    if (!std::isfinite(a->wavelet[n]))
+      return fail(ctx, RTM_ERR_ARG, "wavelet sample %d is not finite", n);
+  return RTM_OK;
+}
+
+int check_opts(rtm_ctx *ctx, const rtm_opts *o) {
+  if (!o) return fail(ctx, RTM_ERR_ARG, "options are NULL");
+  if (o->isnap < 1) return fail(ctx, RTM_ERR_ARG, "isnap must be >= 1 (got %d)", o->isnap);
+  if (o->snap_dtype < 0 || o->snap_dtype > 2)
+    return fail(ctx, RTM_ERR_ARG, "snap_dtype must be 0, 1 or 2 (got %d)", o->snap_dtype);
+  if (!(o->eps >= 0) || !std::isfinite(o->eps))
+    return fail(ctx, RTM_ERR_ARG, "eps must be finite and >= 0");
+  return RTM_OK;
+}
+
+// Closed form of the stability bound of leapfrog with the 8th-order stencil:
+// v dt sqrt((1/dx^2 + 1/dz^2) * 2048/315) <= 2, 2048/315 being minus the
+// symbol of the 1D weights at the Nyquist wavenumber.
+static double courant_number(double vmax, const rtm_grid &gr) {
+  return vmax * gr.dt * std::sqrt((1.0 / (gr.dx * gr.dx) + 1.0 / (gr.dz * gr.dz)) * 2048.0 / 315.0) /
+         2.0;
+}
+
+int check_velocity(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d, long long n,
+                   cudaStream_t st) {
+  DevBuf r;
+  CU(r.alloc(ctx, 16, st));
+  // pageable copies: the H2D is staged before the call returns and the D2H
+  // completes before it returns, so stack arrays are safe here
+  const unsigned init[4] = {0u, 0x7f7fffffu, 0u, 0u};
+  CU(cudaMemcpyAsync(r.p, init, 16, cudaMemcpyHostToDevice, st));
+  CU(launch_vrange(vel_d, n, r.as<unsigned>(), st));
+  unsigned out[4];
+  CU(cudaMemcpyAsync(out, r.p, 16, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (out[2]) return fail(ctx, RTM_ERR_ARG, "%u velocity values are non-positive or not finite", out[2]);
+  float vmax;
+  std::memcpy(&vmax, &out[0], 4);
+  const double cn = courant_number(vmax, gr);
+  if (cn > 1.0)
+    return fail(ctx, RTM_ERR_CFL,
+                "CFL violated: v_max dt sqrt((1/dx^2+1/dz^2) 2048/315)/2 = %.6f > 1 (v_max=%g)", cn,
+                (double)vmax);
+  return RTM_OK;
+}
+
+// ---------------------------------------------------- memory admission --
+
+size_t reserve_wait(rtm_ctx *ctx, size_t want, size_t min_need, int timeout_ms) {
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto avail = [&]() { return ctx->budget > ctx->used ? ctx->budget - ctx->used : 0; };
+  if (timeout_ms > 0)
+    ctx->mem_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                         [&]() { return avail() >= min_need; });
+  const size_t a = avail();
+  if (a < min_need) return 0;
+  const size_t got = std::min(want, a);
+  ctx->used += got;
+  return got;
+}
+
+void unreserve(rtm_ctx *ctx, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->used = ctx->used > bytes ? ctx->used - bytes : 0;
+  }
+  ctx->mem_cv.notify_all();
+}
+
+// ------------------------------------------------------------- engine --
+
+static void sponge_profile(int N, int nb, std::vector<double> &out) {
+  out.resize(N);
+  for (int I = 0; I < N; ++I) {
+    const int k = std::min(I, N - 1 - I);
+    if (k >= nb) {
+      out[I] = 1.0;
+    } else {
+      const double a = 0.015 * (double)(nb - k);
+      out[I] = std::exp(-a * a);
+    }
+  }
+}
+
+struct Common {
+  Geo g;
+  Coef k;
+  DevBuf c_all, gx, gz, src_rc, rptr, rent, wav, items;
+};
+
+// Upload the per-call tables shared by all items.
+static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
+                        int nsample, const float *vel_d, cudaStream_t st) {
+  C.g = make_geo(gr);
+  C.k = make_coef(gr);
+  const Geo &g = C.g;
+  std::vector<double> pz, px;
+  sponge_profile(g.NZ, g.nb, pz);
+  sponge_profile(g.NX, g.nb, px);
+  std::vector<float> gz(g.NZ), gx(g.P, 0.f);
+  for (int I = 0; I < g.NZ; ++I) gz[I] = (float)pz[I];
+  for (int J = 0; J < g.NX; ++J) gx[g.X0 + J] = (float)px[J];
+  // sources: memory (row, col); receivers: CSR over step-kernel tiles
+  std::vector<int> src(2 * acq.nshot);
+  for (int s = 0; s < acq.nshot; ++s) {
+    src[s] = acq.src_iz[s] + g.nb;
+    src[acq.nshot + s] = acq.src_ix[s] + g.CP;
+  }
+  const int ntiles = g.ntx * g.ntz;
+  std::vector<int> rptr(ntiles + 1, 0);
+  std::vector<int> rtile(acq.nrec);
+  for (int r = 0; r < acq.nrec; ++r) {
+    const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
+    rtile[r] = (row / TZ) * g.ntx + col / TX;
+    rptr[rtile[r] + 1]++;
+  }
+  for (int t = 0; t < ntiles; ++t) rptr[t + 1] += rptr[t];
+  std::vector<int2> rent(std::max(acq.nrec, 1));
+  {
+    std::vector<int> fill(rptr.begin(), rptr.end() - 1);
+    for (int r = 0; r < acq.nrec; ++r) {
+      const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
+      const int t = rtile[r];
+      const int lr = row - (t / g.ntx) * TZ, lc = col - (t % g.ntx) * TX;
+      rent[fill[t]++] = make_int2(lr * TX + lc, r);
+    }
+  }
+  CU(C.c_all.alloc(ctx, (size_t)nsample * g.plane * 4, st));
+  CU(C.gx.alloc(ctx, gx.size() * 4, st));
+  CU(C.gz.alloc(ctx, gz.size() * 4, st));
+  CU(C.src_rc.alloc(ctx, src.size() * 4, st));
+  CU(C.rptr.alloc(ctx, rptr.size() * 4, st));
+  CU(C.rent.alloc(ctx, rent.size() * sizeof(int2), st));
+  CU(C.wav.alloc(ctx, (size_t)gr.nt * 4, st));
+  CU(cudaMemcpyAsync(C.gx.p, gx.data(), gx.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.gz.p, gz.data(), gz.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.src_rc.p, src.data(), src.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.rptr.p, rptr.data(), rptr.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.rent.p, rent.data(), rent.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                     st));
+  CU(cudaMemcpyAsync(C.wav.p, acq.wavelet, (size_t)gr.nt * 4, cudaMemcpyHostToDevice, st));
+  CU(launch_prep_c(vel_d, C.c_all.as<float>(), g, gr.dt, nsample, st));
+  // the host vectors above go out of scope: make the copies complete first
+  CU(cudaStreamSynchronize(st));
+  return RTM_OK;
+}
+
+static void fill_args(StepArgs &A, const Common &C, const rtm_grid &gr, const rtm_acq &acq) {
+  std::memset(&A, 0, sizeof(A));
+  A.g = C.g;
+  A.k = C.k;
+  A.gx = C.gx.as<float>();
+  A.gz = C.gz.as<float>();
+  A.c_all = C.c_all.as<float>();
+  A.src_row = C.src_rc.as<int>();
+  A.src_col = C.src_rc.as<int>() + acq.nshot;
+  A.wav = C.wav.as<float>();
+  A.src_scale = (float)(1.0 / (gr.dx * gr.dz));
+  A.rtile_ptr = C.rptr.as<int>();
+  A.rtile_ent = C.rent.as<int2>();
+  A.nrec = acq.nrec;
+  A.nt = gr.nt;
+}
+
+int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
+                   const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
+                   int B, cudaStream_t st) {
+  Common C;
+  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st);
+  if (rc) return rc;
+  const Geo &g = C.g;
+  const int nsnap = gr.nt / op.isnap;
+  const long long nitems = (long long)nsample * acq.nshot;
+  if (B > nitems) B = (int)nitems;
+  if (B < 1) B = 1;
+  // items in (sample, shot) order
+  std::vector<int> items(2 * nitems);
+  for (long long q = 0; q < nitems; ++q) {
+    items[q] = (int)(q / acq.nshot);
+    items[nitems + q] = (int)(q % acq.nshot);
+  }
+  CU(C.items.alloc(ctx, items.size() * 4, st));
+  CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
+  DevBuf fa, fb, snap, smax, num, den, dmax, stack, comp;
+  const size_t esz = snap_elem_bytes(op.snap_dtype);
+  CU(fa.alloc(ctx, (size_t)B * g.plane * 4, st));
+  CU(fb.alloc(ctx, (size_t)B * g.plane * 4, st));
+  CU(snap.alloc(ctx, std::max<size_t>((size_t)B * nsnap * g.pplane * esz, 16), st));
+  CU(smax.alloc(ctx, (size_t)B * std::max(nsnap, 1) * 4, st));
+  CU(num.alloc(ctx, (size_t)B * g.pplane * 4, st));
+  CU(den.alloc(ctx, (size_t)B * g.pplane * 4, st));
+  CU(dmax.alloc(ctx, (size_t)B * 4, st));
+  CU(stack.alloc(ctx, (size_t)nsample * g.pplane * 4, st));
+  CU(comp.alloc(ctx, (size_t)nsample * g.pplane * 4, st));
+  CU(cudaMemsetAsync(num.p, 0, num.bytes, st));
+  CU(cudaMemsetAsync(den.p, 0, den.bytes, st));
+  CU(cudaMemsetAsync(stack.p, 0, stack.bytes, st));
+  CU(cudaMemsetAsync(comp.p, 0, comp.bytes, st));
+
+  // algorithmic bytes per item (16 B per padded update; b per physical pixel
+  // per snapshot written or read; 16 B per physical pixel per imaging step)
+  const double upd = (double)g.NZ * g.NX, pix = (double)g.nz * g.nx;
+  const int fwd_snaps = (gr.nt - 1) / op.isnap;
+  const double fwd_bytes = gr.nt * 16.0 * upd + fwd_snaps * (double)esz * pix;
+  const double bwd_bytes = gr.nt * 16.0 * upd + nsnap * ((double)esz + 16.0) * pix;
+  long long launches = 0, step_launches = 0;
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() -> int {
+    if (!ctx->prof) return RTM_OK;
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    CU(cudaEventRecord(e, st));
+    ev.push_back(e);
+    return RTM_OK;
+  };
+
+  StepArgs A;
+  fill_args(A, C, gr, acq);
+  A.seis = seis_d;
+  A.snap = snap.p;
+  A.snap_dtype = op.snap_dtype;
+  A.nsnap = nsnap;
+  A.smax = smax.as<unsigned>();
+  A.num = num.as<float>();
+  A.den = den.as<float>();
+  A.dmax = dmax.as<unsigned>();
+  const int isnap = op.isnap, nt = gr.nt;
+  for (long long q0 = 0; q0 < nitems; q0 += B) {
+    const int nb = (int)std::min<long long>(B, nitems - q0);
+    A.item_sample = C.items.as<int>() + q0;
+    A.item_shot = C.items.as<int>() + nitems + q0;
+    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
+    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    CU(cudaMemsetAsync(smax.p, 0, smax.bytes, st));
+    CU(cudaMemsetAsync(dmax.p, 0, dmax.bytes, st));
+    A.fa = fa.as<float>();
+    A.fb = fb.as<float>();
+    StepRT rt{};
+    if ((rc = mark())) return rc;
+    for (int n = 0; n < nt; ++n) {
+      rt.n = n;
+      rt.snap_idx = (n >= isnap && n % isnap == 0) ? n / isnap - 1 : -1;
+      rt.max_idx = (op.snap_dtype != RTM_SNAP_F32 && (n + 1) % isnap == 0) ? (n + 1) / isnap - 1 : -1;
+      rt.img_idx = -1;
+      rt.dmax_flag = 0;
+      CU(launch_step(MODE_FWD, A, rt, nb, st));
+      std::swap(A.fa, A.fb);
+    }
+    if ((rc = mark())) return rc;
+    if (nt % isnap == 0) {
+      CU(launch_snap_store(A, A.fa, nt / isnap - 1, nb, st));
+      ++launches;
+    }
+    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
+    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    if ((rc = mark())) return rc;
+    for (int k = nt; k >= 1; --k) {
+      rt.n = k;
+      rt.snap_idx = -1;
+      rt.max_idx = -1;
+      rt.img_idx = (k % isnap == 0) ? k / isnap - 1 : -1;
+      rt.dmax_flag = (k == isnap) ? 1 : 0;
+      CU(launch_step(MODE_BWD, A, rt, nb, st));
+      std::swap(A.fa, A.fb);
+    }
+    if ((rc = mark())) return rc;
+    CU(launch_norm_stack(A.num, A.den, A.dmax, A.item_sample, nb, (float)op.eps, g.pplane,
+                         stack.as<float>(), comp.as<float>(), st));
+    launches += 2 * (long long)nt + 1;
+    step_launches += 2 * (long long)nt;
+  }
+  CU(launch_filter(stack.as<float>(), comp.as<float>(), nsample, g.nz, g.nx, g.SX,
+                   (float)(1.0 / (gr.dz * gr.dz)), (float)(1.0 / (gr.dx * gr.dx)), op.laplacian,
+                   img_d, st));
+  launches += 2;  // prep_c, filter
+  double ms_total = 0.0;
+  if (ctx->prof) {
+    CU(cudaStreamSynchronize(st));
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      ms_total += ms;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stats.launches += launches;
+    if (ctx->prof) {
+      ctx->stats.step_launches += step_launches;
+      ctx->stats.step_ms += ms_total;
+      ctx->stats.step_bytes += (double)nitems * (fwd_bytes + bwd_bytes);
+      ctx->stats.point_updates += (double)nitems * 2.0 * gr.nt * upd;
+    }
+    ctx->stats.migrations += nitems;
+  }
+  return RTM_OK;
+}
+
+// Forward modelling of shots [s0, s0 + ns) into seis_d [ns][nt][nrec]
+// (device), B shots advanced per launch.
+static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
+                        const rtm_acq &acq, int s0, int ns, float *seis_d, int B,
+                        cudaStream_t st) {
+  Common C;
+  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st);
+  if (rc) return rc;
+  const Geo &g = C.g;
+  if (B > ns) B = ns;
+  if (B < 1) B = 1;
+  std::vector<int> items(2 * (size_t)ns);
+  for (int q = 0; q < ns; ++q) {
+    items[q] = 0;
+    items[ns + q] = s0 + q;
+  }
+  CU(C.items.alloc(ctx, items.size() * 4, st));
+  CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
+  DevBuf fa, fb;
+  CU(fa.alloc(ctx, (size_t)B * g.plane * 4, st));
+  CU(fb.alloc(ctx, (size_t)B * g.plane * 4, st));
+  StepArgs A;
+  fill_args(A, C, gr, acq);
+  long long launches = 0;
+  for (int q0 = 0; q0 < ns; q0 += B) {
+    const int nb = std::min(B, ns - q0);
+    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
+    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    A.item_sample = C.items.as<int>() + q0;
+    A.item_shot = C.items.as<int>() + ns + q0;
+    A.fa = fa.as<float>();
+    A.fb = fb.as<float>();
+    A.rec_out = seis_d + (size_t)q0 * gr.nt * acq.nrec;
+    StepRT rt{};
+    rt.snap_idx = rt.max_idx = rt.img_idx = -1;
+    for (int n = 0; n < gr.nt; ++n) {
+      rt.n = n;
+      CU(launch_step(MODE_MODEL, A, rt, nb, st));
+      std::swap(A.fa, A.fb);
+    }
+    launches += gr.nt;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->stats.launches += launches + 1;
+  return RTM_OK;
+}
+
+// Device view of a caller array: the pointer itself, or a staged copy.
+struct View {
+  DevBuf buf;
+  float *d = nullptr;
+  bool staged = false;
+};
+
+static int view_in(rtm_ctx *ctx, View &v, const float *p, size_t bytes, cudaStream_t st) {
+  if (is_device_ptr(p)) {
+    v.d = const_cast<float *>(p);
+    return RTM_OK;
+  }
+  CU(v.buf.alloc(ctx, bytes, st));
+  CU(cudaMemcpyAsync(v.buf.p, p, bytes, cudaMemcpyHostToDevice, st));
+  v.d = v.buf.as<float>();
+  v.staged = true;
+  return RTM_OK;
+}
+
+static int view_out(rtm_ctx *ctx, View &v, float *p, size_t bytes, cudaStream_t st) {
+  if (is_device_ptr(p)) {
+    v.d = p;
+    return RTM_OK;
+  }
+  CU(v.buf.alloc(ctx, bytes, st));
+  v.d = v.buf.as<float>();
+  v.staged = true;
+  return RTM_OK;
+}
+
+static int view_finish(rtm_ctx *ctx, View &v, float *p, size_t bytes, cudaStream_t st) {
+  if (!v.staged) return RTM_OK;
+  CU(cudaMemcpyAsync(p, v.d, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return RTM_OK;
+}
+
+static int set_device(rtm_ctx *ctx) {
+  CU(cudaSetDevice(ctx->device));
+  return RTM_OK;
+}
+
+}  // namespace rtm
+
+using namespace rtm;
+
+// ------------------------------------------------------------------ ABI --
+
+extern "C" {
+
+double rtm_cfl_limit(void) { return 2.0 / std::sqrt(2.0 * 2048.0 / 315.0); }
+
+int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
+  if (!out) return RTM_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return RTM_ERR_ARG;
+  }
+  rtm_ctx *ctx = new rtm_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return RTM_ERR_CUDA;
+  }
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    delete ctx;
+    return RTM_ERR_CUDA;
+  }
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.85 * (double)fr);
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) {
+    delete ctx;
+    return RTM_ERR_CUDA;
+  }
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  *out = ctx;
+  return RTM_OK;
+}
+
+int rtm_ctx_destroy(rtm_ctx *ctx) {
+  if (!ctx) return RTM_OK;
+  cudaSetDevice(ctx->device);
+  rtm_server_shutdown(ctx);
+  cudaDeviceSynchronize();
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+  return RTM_OK;
+}
+
+int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items) {
+  if (!ctx) return RTM_ERR_ARG;
+  if (max_items < 0) return fail(ctx, RTM_ERR_ARG, "max_items must be >= 0");
+  ctx->max_batch = max_items;
+  return RTM_OK;
+}
+
+int rtm_ctx_set_profiling(rtm_ctx *ctx, int on) {
+  if (!ctx) return RTM_ERR_ARG;
+  ctx->prof = on != 0;
+  return RTM_OK;
+}
+
+int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset) {
+  if (!ctx || !out) return RTM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *out = ctx->stats;
+  if (reset) ctx->stats = rtm_stats{};
+  return RTM_OK;
+}
+
+const char *rtm_last_error(rtm_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq, int shot,
+              float *seis, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true))) return rc;
+  if (!vel || !seis) return fail(ctx, RTM_ERR_ARG, "vel and seis must not be NULL");
+  if (shot < -1 || shot >= acq->nshot)
+    return fail(ctx, RTM_ERR_ARG, "shot %d outside [-1, %d)", shot, acq->nshot);
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int s0 = shot < 0 ? 0 : shot, ns = shot < 0 ? acq->nshot : 1;
+  const size_t vbytes = (size_t)grid->nx * grid->nz * 4;
+  const size_t sbytes = (size_t)ns * grid->nt * acq->nrec * 4;
+  const Geo g = make_geo(*grid);
+  const size_t item = 2 * (size_t)g.plane * 4;
+  const size_t io = (is_device_ptr(vel) ? 0 : vbytes) + (is_device_ptr(seis) ? 0 : sbytes);
+  const size_t base = (size_t)g.plane * 4 + (size_t)(g.P + g.NZ) * 4 + (size_t)acq->nrec * 12 +
+                      (size_t)acq->nshot * 16 + (size_t)grid->nt * 4 + (size_t)(g.ntx * g.ntz + 1) * 4 +
+                      io + 4096;
+  if (base + item > ctx->budget)
+    return fail(ctx, RTM_ERR_NOMEM, "modelling needs %.3f GB, budget is %.3f GB", (base + item) / 1e9,
+                ctx->budget / 1e9);
+  size_t want = base + (size_t)ns * item;
+  if (ctx->max_batch > 0) want = std::min(want, base + (size_t)ctx->max_batch * item);
+  const size_t got = reserve_wait(ctx, want, base + item, 600000);
+  if (!got) return fail(ctx, RTM_ERR_TIMEOUT, "waited 600 s for device memory");
+  const int B = (int)std::max<size_t>(1, std::min<size_t>(ns, (got - base) / item));
+  View v, s;
+  rc = view_in(ctx, v, vel, vbytes, st);
+  if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)grid->nx * grid->nz, st);
+  if (!rc) rc = view_out(ctx, s, seis, sbytes, st);
+  if (!rc) rc = model_device(ctx, *grid, v.d, *acq, s0, ns, s.d, B, st);
+  if (!rc) rc = view_finish(ctx, s, seis, sbytes, st);
+  unreserve(ctx, got);
+  return rc;
+}
+
+static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const float *vels,
+                          const rtm_acq *acq, const float *seis, const rtm_opts *opts,
+                          float *images, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true)) ||
+      (rc = check_opts(ctx, opts)))
+    return rc;
+  if (nsample < 1) return fail(ctx, RTM_ERR_ARG, "nsample must be >= 1");
+  if (!vels || !seis || !images) return fail(ctx, RTM_ERR_ARG, "NULL array argument");
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vbytes = (size_t)nsample * grid->nx * grid->nz * 4;
+  const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
+  const MigrationPlan plan = plan_migration(*grid, *acq, *opts, nsample);
+  const size_t io = (is_device_ptr(vels) ? 0 : vbytes) + (is_device_ptr(seis) ? 0 : sbytes) +
+                    (is_device_ptr(images) ? 0 : vbytes);
+  const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
+  const long long nitems = (long long)nsample * acq->nshot;
+  size_t want = plan.shared_bytes + io + (size_t)nitems * plan.item_bytes;
+  if (ctx->max_batch > 0)
+    want = std::min(want, plan.shared_bytes + io + (size_t)ctx->max_batch * plan.item_bytes);
+  if (need1 > ctx->budget)
+    return fail(ctx, RTM_ERR_NOMEM, "one migration needs %.3f GB, budget is %.3f GB",
+                need1 / 1e9, ctx->budget / 1e9);
+  const size_t got = reserve_wait(ctx, want, need1, 600000);
+  if (!got) return fail(ctx, RTM_ERR_TIMEOUT, "waited 600 s for %.3f GB of the budget", need1 / 1e9);
+  // items in flight: what the reservation holds, balanced over the batches
+  long long bmax = std::max<long long>(
+      1, std::min<long long>(nitems, (long long)((got - plan.shared_bytes - io) / plan.item_bytes)));
+  const long long nbatch = (nitems + bmax - 1) / bmax;
+  const int B = (int)((nitems + nbatch - 1) / nbatch);
+  View v, s, im;
+  rc = view_in(ctx, v, vels, vbytes, st);
+  if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
+  if (!rc) rc = view_in(ctx, s, seis, sbytes, st);
+  if (!rc) rc = view_out(ctx, im, images, vbytes, st);
+  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, *opts, im.d, B, st);
+  if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
+  unreserve(ctx, got);
+  return rc;
+}
+
+int rtm_migrate(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,
+                const float *seis, const rtm_opts *opts, float *image, void *stream) {
+  return migrate_common(ctx, grid, 1, vel, acq, seis, opts, image, stream);
+}
+
+int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const float *vels,
+                         const rtm_acq *acq, const float *seis, const rtm_opts *opts,
+                         float *images, void *stream) {
+  return migrate_common(ctx, grid, nsample, vels, acq, seis, opts, images, stream);
+}
+
+int rtm_ensemble_stats(rtm_ctx *ctx, const float *images, int n, long npix, double *mean,
+                       double *std_, float *q05, float *q95, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  if (!images || !mean || !std_ || !q05 || !q95) return fail(ctx, RTM_ERR_ARG, "NULL array argument");
+  if (n < 1 || n > ens_stats_max_n() || npix < 1)
+    return fail(ctx, RTM_ERR_ARG, "need 1 <= n <= %d and npix >= 1 (n=%d npix=%ld)",
+                ens_stats_max_n(), n, npix);
+  int rc;
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(images) && is_device_ptr(mean) && is_device_ptr(std_) &&
+                   is_device_ptr(q05) && is_device_ptr(q95);
+  if (dev) {
+    CU(launch_ens_stats(images, n, npix, mean, std_, q05, q95, st));
+    return RTM_OK;
+  }
+  DevBuf bi, bm, bs, b5, b9;
+  CU(bi.alloc(ctx, (size_t)n * npix * 4, st));
+  CU(bm.alloc(ctx, (size_t)npix * 8, st));
+  CU(bs.alloc(ctx, (size_t)npix * 8, st));
+  CU(b5.alloc(ctx, (size_t)npix * 4, st));
+  CU(b9.alloc(ctx, (size_t)npix * 4, st));
+  CU(cudaMemcpyAsync(bi.p, images, bi.bytes, cudaMemcpyDefault, st));
+  CU(launch_ens_stats(bi.as<float>(), n, npix, bm.as<double>(), bs.as<double>(), b5.as<float>(),
+                      b9.as<float>(), st));
+  CU(cudaMemcpyAsync(mean, bm.p, bm.bytes, cudaMemcpyDefault, st));
+  CU(cudaMemcpyAsync(std_, bs.p, bs.bytes, cudaMemcpyDefault, st));
+  CU(cudaMemcpyAsync(q05, b5.p, b5.bytes, cudaMemcpyDefault, st));
+  CU(cudaMemcpyAsync(q95, b9.p, b9.bytes, cudaMemcpyDefault, st));
+  CU(cudaStreamSynchronize(st));
+  return RTM_OK;
+}
+
+int rtm_uncertainty_maps(rtm_ctx *ctx, const double *mean, const double *std_, long npix,
+                         double *conf, double *ratio, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  if (!mean || !std_ || !conf || !ratio || npix < 1) return fail(ctx, RTM_ERR_ARG, "bad arguments");
+  int rc;
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf scratch;
+  CU(scratch.alloc(ctx, 16, st));
+  const bool dev = is_device_ptr(mean) && is_device_ptr(std_) && is_device_ptr(conf) &&
+                   is_device_ptr(ratio);
+  if (dev) {
+    CU(launch_unc_maps(mean, std_, npix, conf, ratio, scratch.as<unsigned long long>(), st));
+    return RTM_OK;
+  }
+  DevBuf bm, bs, bc, br;
+  CU(bm.alloc(ctx, (size_t)npix * 8, st));
+  CU(bs.alloc(ctx, (size_t)npix * 8, st));
+  CU(bc.alloc(ctx, (size_t)npix * 8, st));
+  CU(br.alloc(ctx, (size_t)npix * 8, st));
+  CU(cudaMemcpyAsync(bm.p, mean, bm.bytes, cudaMemcpyDefault, st));
+  CU(cudaMemcpyAsync(bs.p, std_, bs.bytes, cudaMemcpyDefault, st));
+  CU(launch_unc_maps(bm.as<double>(), bs.as<double>(), npix, bc.as<double>(), br.as<double>(),
+                     scratch.as<unsigned long long>(), st));
+  CU(cudaMemcpyAsync(conf, bc.p, bc.bytes, cudaMemcpyDefault, st));
+  CU(cudaMemcpyAsync(ratio, br.p, br.bytes, cudaMemcpyDefault, st));
+  CU(cudaStreamSynchronize(st));
+  return RTM_OK;
+}
+
+int rtm_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket) {
+  if (!ctx) return RTM_ERR_ARG;
+  return rtm_server_submit(ctx, req, ticket);
+}
+
+int rtm_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms) {
+  if (!ctx) return RTM_ERR_ARG;
+  return rtm_server_poll(ctx, ticket, state, timeout_ms);
+}
+
+}  // extern "C"

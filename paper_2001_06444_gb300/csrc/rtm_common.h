@@ -1,0 +1,77 @@
+// rtm_common.h — structures shared by the host runtime and the kernels.
+//
+// Memory layout of one propagation grid (one velocity sample x one shot):
+//   rows    I in [0, NZ), NZ = nz + 2 nb (padded, sponge on both sides);
+//   columns stored at memory column X0 + J for padded column J in [0, NX),
+//   NX = nx + 2 nb, with X0 = (4 - nb % 4) % 4 so that the first physical
+//   column (memory column CP = X0 + nb) is 16-byte aligned;
+//   row pitch P floats (multiple of 32, i.e. 128-byte rows);
+//   every column outside [X0, X0 + NX) holds zero forever, which realises the
+//   zero field beyond the padded domain.
+// Physical-grid arrays (snapshots, imaging accumulators, stacks) are
+// [nz][SX] with SX = nx rounded up to 4, column j at offset j.
+#pragma once
+#include <cstdint>
+
+namespace rtm {
+
+constexpr int TX = 128;   // tile width  (memory columns) of the step kernel
+constexpr int TZ = 32;    // tile height (rows)
+constexpr int HALO = 4;   // stencil radius (8th order)
+constexpr int SW = TX + 2 * HALO;
+constexpr int SH = TZ + 2 * HALO;
+constexpr int STEP_THREADS = 256;  // 32 x 8: 4 columns x 4 rows per thread
+
+struct Geo {
+  int NZ, P, X0, NX, nb;  // padded grid
+  int nz, nx, SX, CP;     // physical grid and its memory column origin
+  int ntx, ntz;           // tiles per grid
+  long long plane;        // NZ * P   (floats)
+  long long pplane;       // nz * SX  (elements)
+};
+
+struct Coef {
+  float c0;     // a0 (1/dx^2 + 1/dz^2)
+  float ax[4];  // a_m / dx^2
+  float az[4];  // a_m / dz^2
+};
+
+// Arguments of one batched launch over B items (blockIdx.z = item slot).
+struct StepArgs {
+  Geo g;
+  Coef k;
+  const float *gx, *gz;      // sponge factors per memory column / row
+  const float *c_all;        // [nsample][plane]  (v dt)^2, zero outside
+  const int *item_sample;    // [B]
+  const int *item_shot;      // [B]
+  float *fa;                 // [B][plane] current field (read)
+  float *fb;                 // [B][plane] previous field, overwritten with the new one
+  const int *src_row, *src_col;  // [nshot] memory coordinates of each source
+  const float *wav;          // [nt] wavelet
+  float src_scale;           // 1 / (dx dz)
+  const int *rtile_ptr;      // [ntx*ntz + 1] receivers per tile (CSR)
+  const int2 *rtile_ent;     // {local offset (row*TX + col), receiver index}
+  int nrec, nt;
+  const float *seis;         // [nshot][nt][nrec] data injected backward
+  float *rec_out;            // [B][nt][nrec] recorded traces (modelling)
+  void *snap;                // [B][nsnap][nz][SX] stored source snapshots
+  int snap_dtype;            // 0 f32, 1 bf16, 2 f16
+  int nsnap;
+  unsigned *smax;            // [B][nsnap] max |S^k| as float bits
+  float *num, *den;          // [B][pplane] imaging accumulators
+  unsigned *dmax;            // [B] max of den as float bits
+};
+
+// Per-launch scalars.
+struct StepRT {
+  int n;          // forward: time index of the update (u^{n+1} produced)
+                  // backward: k of the produced field w^k
+  int snap_idx;   // forward: store the CURRENT field u^n as snapshot snap_idx (-1 none)
+  int max_idx;    // forward: reduce max |u^{n+1}| into slot max_idx (-1 none)
+  int img_idx;    // backward: image with snapshot img_idx (-1 none)
+  int dmax_flag;  // backward: after imaging, reduce max(den) into dmax
+};
+
+enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2 };
+
+}  // namespace rtm

@@ -1,0 +1,37 @@
+// rtm_launch.h — host-side launchers of the kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "rtm_common.h"
+
+namespace rtm {
+
+// propagation (rtm_prop.cu)
+cudaError_t launch_step(int mode, const StepArgs &A, const StepRT &rt, int B, cudaStream_t st);
+cudaError_t launch_snap_store(const StepArgs &A, const float *field, int idx, int B,
+                              cudaStream_t st);
+cudaError_t launch_prep_c(const float *vel, float *c_all, const Geo &g, double dt, int nsample,
+                          cudaStream_t st);
+cudaError_t launch_vrange(const float *v, long long n, unsigned *out, cudaStream_t st);
+
+// imaging and statistics (rtm_post.cu)
+// Normalise each item's image (Eq. 5 with eps max(den)) and add it, in item
+// order, to its sample's Kahan-compensated stack; zero num and den.
+cudaError_t launch_norm_stack(float *num, float *den, const unsigned *dmax,
+                              const int *item_sample, int B, float eps, long long pplane,
+                              float *stack_all, float *comp_all, cudaStream_t st);
+// Final image of nsample samples: (optionally) the Laplacian filter of the
+// compensated stack, written compactly as [nsample][nz][nx].
+cudaError_t launch_filter(const float *stack_all, const float *comp_all, int nsample, int nz,
+                          int nx, int SX, float rdz2, float rdx2, int laplacian, float *out,
+                          cudaStream_t st);
+// Per-pixel ensemble statistics.
+cudaError_t launch_ens_stats(const float *images, int n, long long npix, double *mean,
+                             double *std_, float *q05, float *q95, cudaStream_t st);
+// Eq. 6 / Eq. 7 maps; scratch must hold 2 unsigned long long.
+cudaError_t launch_unc_maps(const double *mean, const double *std_, long long npix,
+                            double *conf, double *ratio, unsigned long long *scratch,
+                            cudaStream_t st);
+int ens_stats_max_n();
+
+}  // namespace rtm

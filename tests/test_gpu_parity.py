@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances: seismograms 1e-4 relative L2, images 1e-3 with FP32 snapshots
+and 1e-2 with half-precision snapshots; source and receiver indexing
+bit-exact.  Inputs are generated once, rounded to float32, and given to both
+sides; the oracle never sees anything the GPU computed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_l2
+from paper_2001_06444_gb300 import inputs
+from paper_2001_06444_gb300 import rtm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEIS_TOL, IMG_TOL, HALF_IMG_TOL = 1e-4, 1e-3, 1e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rtm.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.ascontiguousarray(np.asarray(a, np.float32))
+
+
+def dev(a):
+    return torch.from_numpy(f32(a)).cuda()
+
+
+def gpu_model(ctx, s, vel, shot=0, rec=None):
+    rec_ix, rec_iz = (s.rec_ix, s.rec_iz) if rec is None else rec
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, rec_ix, rec_iz, f32(s.wavelet))
+    out = torch.zeros((s.nt, np.size(rec_ix)), dtype=torch.float32, device="cuda")
+    ctx.model(rtm.make_grid(*s.grid_tuple()), dev(vel), acq, shot, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def ora_model(s, vel, shot=0, rec=None):
+    rec_ix, rec_iz = (s.rec_ix, s.rec_iz) if rec is None else rec
+    return oracle.model(oracle.grid(*s.grid_tuple()), f32(vel).astype(np.float64),
+                        s.src_ix[shot], s.src_iz[shot], rec_ix, rec_iz,
+                        f32(s.wavelet).astype(np.float64))
+
+
+def gpu_migrate(ctx, s, vel, seis, isnap=1, dtype=rtm.SNAP_F32, lap=True, batch=0):
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    ctx.set_batch(batch)
+    ctx.migrate(rtm.make_grid(*s.grid_tuple()), dev(vel), acq, dev(seis),
+                rtm.Opts(isnap, dtype, 1e-6, int(lap)), img)
+    ctx.set_batch(0)
+    torch.cuda.synchronize()
+    return img.cpu().numpy()
+
+
+def ora_migrate(s, vel, seis, isnap=1, mode=0, lap=True):
+    return oracle.migrate(oracle.grid(*s.grid_tuple()), f32(vel).astype(np.float64), s.src_ix,
+                          s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet).astype(np.float64),
+                          f32(seis).astype(np.float64), isnap=isnap, snap_mode=mode, laplacian=lap)
+
+
+@pytest.fixture(scope="module")
+def flat():
+    """Flat-reflector workload (201 x 101, 1000 steps) with oracle data."""
+    s = inputs.flat_reflector()
+    d_two = ora_model(s, s.vel)
+    d_dir = ora_model(s, np.full_like(s.vel, 1500.0))
+    return s, f32(d_two - d_dir)
+
+
+def test_flat_reflector_seismogram(ctx, flat):
+    s, _ = flat
+    got = gpu_model(ctx, s, s.vel)
+    want = ora_model(s, s.vel)
+    assert rel_l2(got, want) <= SEIS_TOL
+
+
+def test_flat_reflector_image(ctx, flat):
+    s, data = flat
+    got = gpu_migrate(ctx, s, s.vel, data[None])
+    want = ora_migrate(s, s.vel, data[None])
+    assert rel_l2(got, want) <= IMG_TOL
+
+
+def test_flat_reflector_depth_on_gpu(ctx, flat):
+    from scipy.signal import hilbert
+
+    s, data = flat
+    img = gpu_migrate(ctx, s, np.full_like(s.vel, 1500.0), data[None])
+    prof = img[:, 50:151].astype(np.float64).mean(axis=1)
+    env = np.abs(hilbert(prof))
+    pick = 10 + int(np.argmax(env[10:91]))
+    assert abs(pick * s.dz - 495.0) <= 10.0
+
+
+def test_source_and_receiver_indices_bit_exact(ctx):
+    """After one update the field is non-zero at the source cell only; after
+    two, exactly on the 8th-order cross around it."""
+    nx, nz = 37, 29
+    s = inputs.Survey(nx, nz, 7, 10.0, 10.0, 1e-3, 2, np.full((nz, nx), 2000.0),
+                      np.array([11], np.int32), np.array([17], np.int32),
+                      np.repeat(np.arange(nx), nz).astype(np.int32),
+                      np.tile(np.arange(nz), nx).astype(np.int32),
+                      np.array([1.0, 0.0]))
+    d = gpu_model(ctx, s, s.vel)
+    first = d[0].reshape(nx, nz).T
+    nzr = np.argwhere(first != 0)
+    assert nzr.tolist() == [[17, 11]]
+    second = d[1].reshape(nx, nz).T != 0
+    cross = np.zeros((nz, nx), bool)
+    cross[17, 11 - 4:11 + 5] = True
+    cross[17 - 4:17 + 5, 11] = True
+    assert np.array_equal(second, cross)
+
+
+@pytest.mark.parametrize("nx,nz,nb,dx,dz", [(300, 75, 20, 10.0, 10.0), (263, 141, 13, 8.0, 12.0),
+                                             (130, 40, 3, 10.0, 10.0)])
+def test_ragged_grids_model_and_migrate(ctx, nx, nz, nb, dx, dz):
+    """Several tiles with ragged tails, sponge widths that are not multiples of
+    4 (unaligned padded origin), rectangular cells, three shots."""
+    nt = 400
+    v = inputs.layered_faulted(nz, nx, dx, dz, seed=77, water_depth=60.0)
+    s = inputs.Survey(nx, nz, nb, dx, dz, 1e-3, nt, v,
+                      np.array([5, nx // 2, nx - 3], np.int32), np.array([1, 2, 0], np.int32),
+                      np.arange(0, nx, 2, dtype=np.int32), np.full((nx + 1) // 2, 1, np.int32),
+                      inputs.ricker(18.0, 1e-3, nt))
+    for shot in range(3):
+        assert rel_l2(gpu_model(ctx, s, v, shot), ora_model(s, v, shot)) <= SEIS_TOL
+    vm = inputs.smooth(v, dx, dz, 40.0)
+    data = np.stack([ora_model(s, v, k) for k in range(3)])
+    assert rel_l2(gpu_migrate(ctx, s, vm, data, isnap=3), ora_migrate(s, vm, data, isnap=3)) <= IMG_TOL
+
+
+def test_batch_size_does_not_change_the_image(ctx, flat):
+    s0, _ = flat
+    nt = 300
+    s = inputs.Survey(s0.nx, s0.nz, 20, 10.0, 10.0, 1e-3, nt, s0.vel,
+                      np.array([20, 60, 100, 140, 180], np.int32), np.full(5, 2, np.int32),
+                      s0.rec_ix, s0.rec_iz, inputs.ricker(15.0, 1e-3, nt))
+    data = np.stack([ora_model(s, s.vel, k) for k in range(5)])
+    a = gpu_migrate(ctx, s, s.vel, data, isnap=2, batch=1)
+    b = gpu_migrate(ctx, s, s.vel, data, isnap=2, batch=2)
+    c = gpu_migrate(ctx, s, s.vel, data, isnap=2, batch=0)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert rel_l2(a, ora_migrate(s, s.vel, data, isnap=2)) <= IMG_TOL
+
+
+@pytest.mark.parametrize("mode", [rtm.SNAP_BF16, rtm.SNAP_F16])
+@pytest.mark.parametrize("isnap", [1, 4, 8])
+def test_half_precision_snapshots(ctx, flat, mode, isnap):
+    s, data = flat
+    got = gpu_migrate(ctx, s, s.vel, data[None], isnap=isnap, dtype=mode)
+    want_q = ora_migrate(s, s.vel, data[None], isnap=isnap, mode=mode)
+    want_x = ora_migrate(s, s.vel, data[None], isnap=isnap, mode=0)
+    assert rel_l2(got, want_q) <= HALF_IMG_TOL
+    assert rel_l2(got, want_x) <= HALF_IMG_TOL
+
+
+def test_reciprocity_fp32(ctx):
+    nx, nz, nt = 160, 90, 500
+    v = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=5, water_depth=100.0)
+    a, b = (12, 3), (141, 70)
+    w = inputs.ricker(15.0, 1e-3, nt)
+
+    def trace(src, rec):
+        s = inputs.Survey(nx, nz, 20, 10.0, 10.0, 1e-3, nt, v, np.array([src[0]], np.int32),
+                          np.array([src[1]], np.int32), np.array([rec[0]], np.int32),
+                          np.array([rec[1]], np.int32), w)
+        return gpu_model(ctx, s, v)[:, 0]
+
+    assert rel_l2(trace(a, b), trace(b, a)) < 1e-5
+
+
+def test_ensemble_matches_single_migrations(ctx):
+    nx, nz, nt = 180, 70, 350
+    base = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=9, water_depth=100.0)
+    ens = inputs.ensemble(base, 10.0, 10.0, 3, water_depth=100.0)
+    s = inputs.Survey(nx, nz, 20, 10.0, 10.0, 1e-3, nt, base, np.array([30, 90, 150], np.int32),
+                      np.full(3, 1, np.int32), np.arange(nx, dtype=np.int32),
+                      np.full(nx, 1, np.int32), inputs.ricker(15.0, 1e-3, nt))
+    data = np.stack([ora_model(s, base, k) for k in range(3)])
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+    imgs = torch.zeros((3, nz, nx), dtype=torch.float32, device="cuda")
+    ctx.migrate_ensemble(rtm.make_grid(*s.grid_tuple()), dev(ens), acq, dev(data),
+                         rtm.Opts(2, rtm.SNAP_F32, 1e-6, 1), imgs)
+    torch.cuda.synchronize()
+    imgs = imgs.cpu().numpy()
+    for k in range(3):
+        single = gpu_migrate(ctx, s, ens[k], data, isnap=2)
+        assert np.array_equal(imgs[k], single)
+        assert rel_l2(imgs[k], ora_migrate(s, ens[k], data, isnap=2)) <= IMG_TOL
+
+
+@pytest.mark.parametrize("n,npix", [(1, 1000), (2, 777), (5, 4099), (64, 12345), (97, 3001),
+                                    (300, 517)])
+def test_ensemble_stats(ctx, n, npix):
+    x = f32(inputs.normal(100 + n, n * npix).reshape(n, npix) * 3.0 + 1.0)
+    out = [torch.zeros(npix, dtype=t, device="cuda")
+           for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    ctx.ensemble_stats(torch.from_numpy(x).cuda(), *out)
+    torch.cuda.synchronize()
+    mean, std, q05, q95 = [o.cpu().numpy() for o in out]
+    m, sd, a, b = oracle.ensemble_stats(x)
+    assert np.allclose(mean, m, rtol=1e-12, atol=1e-13)
+    assert np.allclose(std, sd, rtol=1e-12, atol=1e-13)
+    assert np.array_equal(q05, a.astype(np.float32))
+    assert np.array_equal(q95, b.astype(np.float32))
+
+
+def test_ensemble_stats_host_buffers(ctx):
+    x = f32(inputs.normal(7, 16 * 999).reshape(16, 999))
+    outs = [np.zeros(999, np.float64), np.zeros(999, np.float64), np.zeros(999, np.float32),
+            np.zeros(999, np.float32)]
+    ctx.ensemble_stats(x, *outs)
+    m, sd, a, b = oracle.ensemble_stats(x)
+    assert np.allclose(outs[0], m, rtol=1e-12) and np.allclose(outs[1], sd, rtol=1e-12)
+    assert np.array_equal(outs[2], a.astype(np.float32))
+
+
+def test_uncertainty_maps(ctx):
+    mean = inputs.normal(1, 5000)
+    mean[::7] = 0.0
+    std = np.abs(inputs.normal(2, 5000))
+    c = torch.zeros(5000, dtype=torch.float64, device="cuda")
+    r = torch.zeros(5000, dtype=torch.float64, device="cuda")
+    ctx.uncertainty_maps(torch.from_numpy(mean).cuda(), torch.from_numpy(std).cuda(), c, r)
+    torch.cuda.synchronize()
+    oc, orr = oracle.uncertainty_maps(mean, std)
+    assert np.allclose(c.cpu().numpy(), oc, rtol=1e-14, atol=1e-15)
+    assert np.allclose(r.cpu().numpy(), orr, rtol=1e-14, atol=0)
+
+
+def test_errors_are_reported(ctx, flat):
+    s, data = flat
+    g = rtm.make_grid(*s.grid_tuple())
+    keep = rtm._Keep()
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    bad = rtm.make_acq(keep, [s.nx], [2], s.rec_ix, s.rec_iz, f32(s.wavelet))
+    with pytest.raises(rtm.RTMError) as e:
+        ctx.migrate(g, dev(s.vel), bad, dev(data[None]), rtm.Opts(1, 0, 1e-6, 1), img)
+    assert e.value.code == rtm.RTM_ERR_ARG
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+    fast = np.full_like(s.vel, 1.01 * rtm.cfl_limit() * 10.0 / 1e-3)
+    with pytest.raises(rtm.RTMError) as e:
+        ctx.migrate(g, dev(fast), acq, dev(data[None]), rtm.Opts(1, 0, 1e-6, 1), img)
+    assert e.value.code == rtm.RTM_ERR_CFL
+    with pytest.raises(rtm.RTMError) as e:
+        ctx.migrate(g, dev(s.vel), acq, dev(data[None]), rtm.Opts(0, 0, 1e-6, 1), img)
+    assert e.value.code == rtm.RTM_ERR_ARG
+    small = rtm.Context(0, budget_bytes=1 << 20)
+    with pytest.raises(rtm.RTMError) as e:
+        small.migrate(g, dev(s.vel), acq, dev(data[None]), rtm.Opts(1, 0, 1e-6, 1), img)
+    assert e.value.code == rtm.RTM_ERR_NOMEM
+    small.close()
+
+
+def test_host_buffers_match_device_buffers(ctx, flat):
+    s, data = flat
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+    g = rtm.make_grid(*s.grid_tuple())
+    host_img = np.zeros((s.nz, s.nx), np.float32)
+    ctx.migrate(g, f32(s.vel), acq, f32(data[None]), rtm.Opts(2, 0, 1e-6, 1), host_img)
+    assert np.array_equal(host_img, gpu_migrate(ctx, s, s.vel, data[None], isnap=2))
+
+
+def test_full_size_sampled_parity(ctx):
+    """The 1701 x 351, 5000-step workload in the bench's launch configuration:
+    one shot's seismogram on every 17th receiver and its migrated image
+    (FP32 snapshots every 4 steps) against the oracle."""
+    s = inputs.full_size(nshot=96)
+    shot = 47
+    sub = (s.rec_ix[::17], s.rec_iz[::17])
+    got = gpu_model(ctx, s, s.vel, shot, rec=sub)
+    want = ora_model(s, s.vel, shot, rec=sub)
+    assert rel_l2(got, want) <= SEIS_TOL
+    one = inputs.Survey(s.nx, s.nz, s.nb, s.dx, s.dz, s.dt, s.nt, s.vel, s.src_ix[shot:shot + 1],
+                        s.src_iz[shot:shot + 1], s.rec_ix, s.rec_iz, s.wavelet)
+    data = f32(ora_model(one, s.vel))[None]
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    gi = gpu_migrate(ctx, one, vm, data, isnap=4)
+    oi = ora_migrate(one, vm, data, isnap=4)
+    assert rel_l2(gi, oi) <= IMG_TOL
