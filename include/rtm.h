@@ -156,6 +156,15 @@ int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset);
 int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
               const rtm_acq *acq, int shot, float *seis, void *stream);
 
+/* Device memory a migration needs: *call_bytes once per call (model tables,
+ * stacks) and *item_bytes per (sample, shot) migration in flight (fields,
+ * snapshot store, imaging accumulators).  A call runs with at least one item
+ * in flight, so it needs call_bytes + item_bytes of the context budget; more
+ * items in flight raise throughput.  No device work; RTM_ERR_ARG on bad
+ * arguments. */
+int rtm_plan_bytes(const rtm_grid *grid, const rtm_acq *acq, const rtm_opts *opts,
+                   int nsample, size_t *call_bytes, size_t *item_bytes);
+
 /* Reverse time migration of all shots of acq over one velocity model
  * (§2.2 Eq. 5 imaging, §3 Laplacian on the brute stack; Listing 1 loop).
  * seis: [nshot][nt][nrec] observed data; image: [nz][nx] output (the filtered

@@ -14,9 +14,12 @@
 // This is Listing 1's shot loop (forward modelling, then adjoint modelling
 // with imaging) with the shots and the Monte Carlo samples of §3 run side by
 // side on one GPU instead of in MPI subgroups.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -84,6 +87,8 @@ Geo make_geo(const rtm_grid &gr) {
   g.P = (int)round_up(std::max(g.X0 + g.NX, g.CP + g.SX), 32);
   g.ntx = (g.P + TX - 1) / TX;
   g.ntz = (g.NZ + TZ - 1) / TZ;
+  g.ntx2 = (g.P + step2_tile_x() - 1) / step2_tile_x();
+  g.ntz2 = (g.NZ + step2_tile_z() - 1) / step2_tile_z();
   g.plane = (long long)g.NZ * g.P;
   g.pplane = (long long)g.nz * g.SX;
   return g;
@@ -111,11 +116,12 @@ MigrationPlan plan_migration(const rtm_grid &gr, const rtm_acq &acq, const rtm_o
   p.g = make_geo(gr);
   p.nsnap = gr.nt / op.isnap;
   const Geo &g = p.g;
-  p.item_bytes = 2 * (size_t)g.plane * 4 + (size_t)p.nsnap * g.pplane * snap_elem_bytes(op.snap_dtype) +
+  p.item_bytes = 4 * (size_t)g.plane * 4 + (size_t)p.nsnap * g.pplane * snap_elem_bytes(op.snap_dtype) +
                  2 * (size_t)g.pplane * 4 + (size_t)(p.nsnap + 1) * 4 + 256 * 6;
   p.shared_bytes = (size_t)nsample * g.plane * 4 + (size_t)g.P * 4 + (size_t)g.NZ * 4 +
                    (size_t)acq.nshot * 8 + (size_t)(g.ntx * g.ntz + 1) * 4 +
-                   (size_t)acq.nrec * 8 + (size_t)gr.nt * 4 + 2 * (size_t)nsample * g.pplane * 4 +
+                   (size_t)acq.nrec * 40 + (size_t)(g.ntx2 * g.ntz2 + 1) * 8 + (size_t)gr.nt * 4 +
+                   2 * (size_t)nsample * g.pplane * 4 +
                    (size_t)acq.nshot * (size_t)nsample * 8 + 4096;
   return p;
 }
@@ -236,11 +242,83 @@ static void sponge_profile(int N, int nb, std::vector<double> &out) {
   }
 }
 
+// ------------------------------------------------------- tensor maps --
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// 3D map over [depth][NZ][P] floats with a (bx, bz, 1) box; out-of-range
+// elements of a box read as zero.
+static int make_map(rtm_ctx *ctx, CUtensorMap *m, const float *base, const Geo &g, int depth,
+                    int bx, int bz) {
+  auto fn = encode_fn();
+  if (!fn) return fail(ctx, RTM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.NZ, (cuuint64_t)depth};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.plane * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)bz, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, RTM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return RTM_OK;
+}
+
+// ---------------------------------------------------------------- engine --
+
 struct Common {
   Geo g;
   Coef k;
-  DevBuf c_all, gx, gz, src_rc, rptr, rent, wav, items;
+  DevBuf c_all, gx, gz, src_rc, rptr, rent, rext_ptr, rext_ent, rcen_ptr, rcen_ent, wav, items, err;
+  CUtensorMap mc;
 };
+
+// Receiver lists of the two-step tiles: every tile whose extended region
+// (tile plus a 4-point ring) holds the receiver, and the one tile whose centre
+// does; offsets are r * EX + c within the extended region.
+static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<int> &eptr,
+                                 std::vector<int2> &eent, std::vector<int> &cptr,
+                                 std::vector<int2> &cent) {
+  const int TXc = step2_tile_x(), TZc = step2_tile_z(), H = step2_ext(), EXw = TXc + 2 * H;
+  const int nt2 = g.ntx2 * g.ntz2;
+  std::vector<std::vector<int2>> e(nt2), c(nt2);
+  for (int r = 0; r < acq.nrec; ++r) {
+    const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
+    const int bx = col / TXc, bz = row / TZc;
+    for (int tz = std::max(0, bz - 1); tz <= std::min(g.ntz2 - 1, bz + 1); ++tz)
+      for (int tx = std::max(0, bx - 1); tx <= std::min(g.ntx2 - 1, bx + 1); ++tx) {
+        const int er = row - (tz * TZc - H), ec = col - (tx * TXc - H);
+        if (er < 0 || er >= TZc + 2 * H || ec < 0 || ec >= EXw) continue;
+        const int2 en = make_int2(er * EXw + ec, r);
+        e[tz * g.ntx2 + tx].push_back(en);
+        if (er >= H && er < H + TZc && ec >= H && ec < H + TXc) c[tz * g.ntx2 + tx].push_back(en);
+      }
+  }
+  eptr.assign(nt2 + 1, 0);
+  cptr.assign(nt2 + 1, 0);
+  eent.clear();
+  cent.clear();
+  for (int t = 0; t < nt2; ++t) {
+    eent.insert(eent.end(), e[t].begin(), e[t].end());
+    cent.insert(cent.end(), c[t].begin(), c[t].end());
+    eptr[t + 1] = (int)eent.size();
+    cptr[t + 1] = (int)cent.size();
+  }
+  if (eent.empty()) eent.push_back(make_int2(0, 0));
+  if (cent.empty()) cent.push_back(make_int2(0, 0));
+}
 
 // Upload the per-call tables shared by all items.
 static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
@@ -254,7 +332,7 @@ static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_a
   std::vector<float> gz(g.NZ), gx(g.P, 0.f);
   for (int I = 0; I < g.NZ; ++I) gz[I] = (float)pz[I];
   for (int J = 0; J < g.NX; ++J) gx[g.X0 + J] = (float)px[J];
-  // sources: memory (row, col); receivers: CSR over step-kernel tiles
+  // sources: memory (row, col); receivers: CSR over single-step tiles
   std::vector<int> src(2 * acq.nshot);
   for (int s = 0; s < acq.nshot; ++s) {
     src[s] = acq.src_iz[s] + g.nb;
@@ -279,23 +357,79 @@ static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_a
       rent[fill[t]++] = make_int2(lr * TX + lc, r);
     }
   }
+  std::vector<int> eptr, cptr;
+  std::vector<int2> eent, cent;
+  step2_receiver_lists(g, acq, eptr, eent, cptr, cent);
   CU(C.c_all.alloc(ctx, (size_t)nsample * g.plane * 4, st));
   CU(C.gx.alloc(ctx, gx.size() * 4, st));
   CU(C.gz.alloc(ctx, gz.size() * 4, st));
   CU(C.src_rc.alloc(ctx, src.size() * 4, st));
   CU(C.rptr.alloc(ctx, rptr.size() * 4, st));
   CU(C.rent.alloc(ctx, rent.size() * sizeof(int2), st));
+  CU(C.rext_ptr.alloc(ctx, eptr.size() * 4, st));
+  CU(C.rext_ent.alloc(ctx, eent.size() * sizeof(int2), st));
+  CU(C.rcen_ptr.alloc(ctx, cptr.size() * 4, st));
+  CU(C.rcen_ent.alloc(ctx, cent.size() * sizeof(int2), st));
   CU(C.wav.alloc(ctx, (size_t)gr.nt * 4, st));
+  CU(C.err.alloc(ctx, 16, st));
   CU(cudaMemcpyAsync(C.gx.p, gx.data(), gx.size() * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(C.gz.p, gz.data(), gz.size() * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(C.src_rc.p, src.data(), src.size() * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(C.rptr.p, rptr.data(), rptr.size() * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(C.rent.p, rent.data(), rent.size() * sizeof(int2), cudaMemcpyHostToDevice,
                      st));
+  CU(cudaMemcpyAsync(C.rext_ptr.p, eptr.data(), eptr.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.rext_ent.p, eent.data(), eent.size() * sizeof(int2),
+                     cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.rcen_ptr.p, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(C.rcen_ent.p, cent.data(), cent.size() * sizeof(int2),
+                     cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(C.wav.p, acq.wavelet, (size_t)gr.nt * 4, cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(C.err.p, 0, 16, st));
   CU(launch_prep_c(vel_d, C.c_all.as<float>(), g, gr.dt, nsample, st));
+  if (ctx->step_kernel == 2) {
+    const int H = step2_ext();
+    int rc = make_map(ctx, &C.mc, C.c_all.as<float>(), g, nsample, step2_tile_x() + 2 * H,
+                      step2_tile_z() + 2 * H);
+    if (rc) return rc;
+  }
   // the host vectors above go out of scope: make the copies complete first
   CU(cudaStreamSynchronize(st));
+  return RTM_OK;
+}
+
+// Field buffers of B items: v ping-pong, d ping-pong (the two-step kernel
+// reads d in a halo, so it cannot update it in place; the single-step kernel
+// does, in whichever buffer is current).
+struct Fields {
+  DevBuf v[2], d[2];
+  CUtensorMap mv[2], md[2];
+  int cv = 0, cd = 0;  // index of the current v and d buffer
+};
+
+static int alloc_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int B, cudaStream_t st) {
+  for (int i = 0; i < 2; ++i) {
+    CU(F.v[i].alloc(ctx, (size_t)B * g.plane * 4, st));
+    CU(F.d[i].alloc(ctx, (size_t)B * g.plane * 4, st));
+    if (ctx->step_kernel == 2) {
+      const int H = step2_ext();
+      int rc = make_map(ctx, &F.mv[i], F.v[i].as<float>(), g, B, step2_tile_x() + 4 * H,
+                        step2_tile_z() + 4 * H);
+      if (!rc)
+        rc = make_map(ctx, &F.md[i], F.d[i].as<float>(), g, B, step2_tile_x() + 2 * H,
+                      step2_tile_z() + 2 * H);
+      if (rc) return rc;
+    }
+  }
+  return RTM_OK;
+}
+
+static int zero_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int nb, cudaStream_t st) {
+  for (int i = 0; i < 2; ++i) {
+    CU(cudaMemsetAsync(F.v[i].p, 0, (size_t)nb * g.plane * 4, st));
+    CU(cudaMemsetAsync(F.d[i].p, 0, (size_t)nb * g.plane * 4, st));
+  }
+  F.cv = F.cd = 0;
   return RTM_OK;
 }
 
@@ -314,6 +448,59 @@ static void fill_args(StepArgs &A, const Common &C, const rtm_grid &gr, const rt
   A.rtile_ent = C.rent.as<int2>();
   A.nrec = acq.nrec;
   A.nt = gr.nt;
+}
+
+static void fill_args2(Step2Args &A2, const StepArgs &A, const Common &C) {
+  std::memset(&A2, 0, sizeof(A2));
+  A2.g = A.g;
+  A2.k = A.k;
+  A2.gx = A.gx;
+  A2.gz = A.gz;
+  A2.c_all = A.c_all;
+  A2.item_sample = A.item_sample;
+  A2.item_shot = A.item_shot;
+  A2.src_row = A.src_row;
+  A2.src_col = A.src_col;
+  A2.wav = A.wav;
+  A2.src_scale = A.src_scale;
+  A2.rext_ptr = C.rext_ptr.as<int>();
+  A2.rext_ent = C.rext_ent.as<int2>();
+  A2.rcen_ptr = C.rcen_ptr.as<int>();
+  A2.rcen_ent = C.rcen_ent.as<int2>();
+  A2.nrec = A.nrec;
+  A2.nt = A.nt;
+  A2.seis = A.seis;
+  A2.rec_out = A.rec_out;
+  A2.snap = A.snap;
+  A2.snap_dtype = A.snap_dtype;
+  A2.nsnap = A.nsnap;
+  A2.smax = A.smax;
+  A2.num = A.num;
+  A2.den = A.den;
+  A2.dmax = A.dmax;
+  A2.err = C.err.as<int>();
+}
+
+// One single-step launch: v from the current buffer into the other, d in place.
+static int step1(rtm_ctx *ctx, int mode, StepArgs &A, Fields &F, const StepRT &rt, int nb,
+                 cudaStream_t st) {
+  A.fa = F.v[F.cv].as<float>();
+  A.fb = F.v[1 - F.cv].as<float>();
+  A.fd = F.d[F.cd].as<float>();
+  CU(launch_step(mode, A, rt, nb, st));
+  F.cv = 1 - F.cv;
+  return RTM_OK;
+}
+
+// One two-step launch: both v and d into the other buffers.
+static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields &F,
+                 const Step2RT &rt, int nb, cudaStream_t st) {
+  A2.v_out = F.v[1 - F.cv].as<float>();
+  A2.d_out = F.d[1 - F.cd].as<float>();
+  CU(launch_step2(mode, F.mv[F.cv], F.md[F.cd], C.mc, A2, rt, nb, st));
+  F.cv = 1 - F.cv;
+  F.cd = 1 - F.cd;
+  return RTM_OK;
 }
 
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
@@ -335,10 +522,10 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   }
   CU(C.items.alloc(ctx, items.size() * 4, st));
   CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
-  DevBuf fa, fb, snap, smax, num, den, dmax, stack, comp;
+  Fields F;
+  if ((rc = alloc_fields(ctx, F, g, B, st))) return rc;
+  DevBuf snap, smax, num, den, dmax, stack, comp;
   const size_t esz = snap_elem_bytes(op.snap_dtype);
-  CU(fa.alloc(ctx, (size_t)B * g.plane * 4, st));
-  CU(fb.alloc(ctx, (size_t)B * g.plane * 4, st));
   CU(snap.alloc(ctx, std::max<size_t>((size_t)B * nsnap * g.pplane * esz, 16), st));
   CU(smax.alloc(ctx, (size_t)B * std::max(nsnap, 1) * 4, st));
   CU(num.alloc(ctx, (size_t)B * g.pplane * 4, st));
@@ -354,8 +541,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   // algorithmic bytes per item (16 B per padded update; b per physical pixel
   // per snapshot written or read; 16 B per physical pixel per imaging step)
   const double upd = (double)g.NZ * g.NX, pix = (double)g.nz * g.nx;
-  const int fwd_snaps = (gr.nt - 1) / op.isnap;
-  const double fwd_bytes = gr.nt * 16.0 * upd + fwd_snaps * (double)esz * pix;
+  const double fwd_bytes = gr.nt * 16.0 * upd + nsnap * (double)esz * pix;
   const double bwd_bytes = gr.nt * 16.0 * upd + nsnap * ((double)esz + 16.0) * pix;
   long long launches = 0, step_launches = 0;
   std::vector<cudaEvent_t> ev;
@@ -379,54 +565,89 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   A.den = den.as<float>();
   A.dmax = dmax.as<unsigned>();
   const int isnap = op.isnap, nt = gr.nt;
+  const bool half = op.snap_dtype != RTM_SNAP_F32;
+  const bool two = ctx->step_kernel == 2;
+  auto inK = [&](int m) { return m >= 1 && m <= nt && m % isnap == 0; };
   for (long long q0 = 0; q0 < nitems; q0 += B) {
     const int nb = (int)std::min<long long>(B, nitems - q0);
     A.item_sample = C.items.as<int>() + q0;
     A.item_shot = C.items.as<int>() + nitems + q0;
-    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
-    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    Step2Args A2;
+    fill_args2(A2, A, C);
+    if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
     CU(cudaMemsetAsync(smax.p, 0, smax.bytes, st));
     CU(cudaMemsetAsync(dmax.p, 0, dmax.bytes, st));
-    A.fa = fa.as<float>();
-    A.fb = fb.as<float>();
-    StepRT rt{};
+    // forward: snapshots S^k, k in K
     if ((rc = mark())) return rc;
-    for (int n = 0; n < nt; ++n) {
-      rt.n = n;
-      rt.snap_idx = (n >= isnap && n % isnap == 0) ? n / isnap - 1 : -1;
-      rt.max_idx = (op.snap_dtype != RTM_SNAP_F32 && (n + 1) % isnap == 0) ? (n + 1) / isnap - 1 : -1;
-      rt.img_idx = -1;
-      rt.dmax_flag = 0;
-      CU(launch_step(MODE_FWD, A, rt, nb, st));
-      std::swap(A.fa, A.fb);
+    bool stored = false;  // the current field, if in K, is already stored
+    for (int n = 0; n < nt;) {
+      if (two && n + 2 <= nt && (!half || isnap % 2 == 0)) {
+        Step2RT r;
+        r.t1 = n;
+        r.t2 = n + 1;
+        r.snap_in_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
+        r.snap_mid_idx = (!half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
+        r.snap_out_idx = (!half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
+        r.max_out_idx = (half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
+        r.img_mid_idx = r.img_out_idx = -1;
+        r.dmax_flag = 0;
+        if ((rc = step2(ctx, MODE_FWD, A2, C, F, r, nb, st))) return rc;
+        stored = !half;
+        n += 2;
+      } else {
+        StepRT r{};
+        r.n = n;
+        r.snap_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
+        r.max_idx = (half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
+        r.img_idx = -1;
+        r.dmax_flag = 0;
+        if ((rc = step1(ctx, MODE_FWD, A, F, r, nb, st))) return rc;
+        stored = false;
+        n += 1;
+      }
+      ++step_launches;
     }
     if ((rc = mark())) return rc;
-    if (nt % isnap == 0) {
-      CU(launch_snap_store(A, A.fa, nt / isnap - 1, nb, st));
+    if (inK(nt) && !stored) {
+      CU(launch_snap_store(A, F.v[F.cv].as<float>(), nt / isnap - 1, nb, st));
       ++launches;
     }
-    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
-    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    // backward: receiver wavefield and imaging
+    if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
     if ((rc = mark())) return rc;
-    for (int k = nt; k >= 1; --k) {
-      rt.n = k;
-      rt.snap_idx = -1;
-      rt.max_idx = -1;
-      rt.img_idx = (k % isnap == 0) ? k / isnap - 1 : -1;
-      rt.dmax_flag = (k == isnap) ? 1 : 0;
-      CU(launch_step(MODE_BWD, A, rt, nb, st));
-      std::swap(A.fa, A.fb);
+    for (int k = nt; k >= 1;) {
+      if (two && k >= 2) {
+        Step2RT r;
+        r.t1 = k - 1;
+        r.t2 = k - 2;
+        r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+        r.img_mid_idx = inK(k) ? k / isnap - 1 : -1;
+        r.img_out_idx = inK(k - 1) ? (k - 1) / isnap - 1 : -1;
+        r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
+        if ((rc = step2(ctx, MODE_BWD, A2, C, F, r, nb, st))) return rc;
+        k -= 2;
+      } else {
+        StepRT r{};
+        r.n = k;
+        r.snap_idx = r.max_idx = -1;
+        r.img_idx = inK(k) ? k / isnap - 1 : -1;
+        r.dmax_flag = (k == isnap) ? 1 : 0;
+        if ((rc = step1(ctx, MODE_BWD, A, F, r, nb, st))) return rc;
+        k -= 1;
+      }
+      ++step_launches;
     }
     if ((rc = mark())) return rc;
     CU(launch_norm_stack(A.num, A.den, A.dmax, A.item_sample, nb, (float)op.eps, g.pplane,
                          stack.as<float>(), comp.as<float>(), st));
-    launches += 2 * (long long)nt + 1;
-    step_launches += 2 * (long long)nt;
+    launches += 1;
   }
+  launches += step_launches;
   CU(launch_filter(stack.as<float>(), comp.as<float>(), nsample, g.nz, g.nx, g.SX,
                    (float)(1.0 / (gr.dz * gr.dz)), (float)(1.0 / (gr.dx * gr.dx)), op.laplacian,
                    img_d, st));
   launches += 2;  // prep_c, filter
+  CU(cudaMemcpyAsync(ctx->h_err, C.err.p, 4, cudaMemcpyDeviceToHost, st));
   double ms_total = 0.0;
   if (ctx->prof) {
     CU(cudaStreamSynchronize(st));
@@ -469,30 +690,42 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
   }
   CU(C.items.alloc(ctx, items.size() * 4, st));
   CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
-  DevBuf fa, fb;
-  CU(fa.alloc(ctx, (size_t)B * g.plane * 4, st));
-  CU(fb.alloc(ctx, (size_t)B * g.plane * 4, st));
+  Fields F;
+  if ((rc = alloc_fields(ctx, F, g, B, st))) return rc;
   StepArgs A;
   fill_args(A, C, gr, acq);
+  const bool two = ctx->step_kernel == 2;
   long long launches = 0;
   for (int q0 = 0; q0 < ns; q0 += B) {
     const int nb = std::min(B, ns - q0);
-    CU(cudaMemsetAsync(fa.p, 0, (size_t)nb * g.plane * 4, st));
-    CU(cudaMemsetAsync(fb.p, 0, (size_t)nb * g.plane * 4, st));
+    if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
     A.item_sample = C.items.as<int>() + q0;
     A.item_shot = C.items.as<int>() + ns + q0;
-    A.fa = fa.as<float>();
-    A.fb = fb.as<float>();
     A.rec_out = seis_d + (size_t)q0 * gr.nt * acq.nrec;
-    StepRT rt{};
-    rt.snap_idx = rt.max_idx = rt.img_idx = -1;
-    for (int n = 0; n < gr.nt; ++n) {
-      rt.n = n;
-      CU(launch_step(MODE_MODEL, A, rt, nb, st));
-      std::swap(A.fa, A.fb);
+    Step2Args A2;
+    fill_args2(A2, A, C);
+    for (int n = 0; n < gr.nt;) {
+      if (two && n + 2 <= gr.nt) {
+        Step2RT r;
+        r.t1 = n;
+        r.t2 = n + 1;
+        r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+        r.img_mid_idx = r.img_out_idx = -1;
+        r.dmax_flag = 0;
+        if ((rc = step2(ctx, MODE_MODEL, A2, C, F, r, nb, st))) return rc;
+        n += 2;
+      } else {
+        StepRT r{};
+        r.n = n;
+        r.snap_idx = r.max_idx = r.img_idx = -1;
+        if ((rc = step1(ctx, MODE_MODEL, A, F, r, nb, st))) return rc;
+        n += 1;
+      }
+      ++launches;
     }
-    launches += gr.nt;
   }
+  CU(cudaMemcpyAsync(ctx->h_err, C.err.p, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));  // `items` lives on this stack frame
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->stats.launches += launches + 1;
   return RTM_OK;
@@ -540,6 +773,17 @@ static int set_device(rtm_ctx *ctx) {
   return RTM_OK;
 }
 
+// A kernel whose bounded wait gave up leaves a flag that the call copies to
+// pinned host memory; it is reported by the call itself when that call
+// synchronises, else by the next call on the context.
+static int check_wait_flag(rtm_ctx *ctx) {
+  if (ctx->h_err && *(volatile int *)ctx->h_err) {
+    *ctx->h_err = 0;
+    return fail(ctx, RTM_ERR_TIMEOUT, "a device-side wait gave up in a previous launch");
+  }
+  return RTM_OK;
+}
+
 }  // namespace rtm
 
 using namespace rtm;
@@ -581,6 +825,15 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
   }
   uint64_t thr = UINT64_MAX;
   cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (cudaMallocHost(&ctx->h_err, 16) != cudaSuccess) {
+    cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+    return RTM_ERR_CUDA;
+  }
+  *ctx->h_err = 0;
+  // RTM_STEP_KERNEL=1 restricts propagation to the single-step kernel
+  const char *sk = std::getenv("RTM_STEP_KERNEL");
+  ctx->step_kernel = (sk && sk[0] == '1') ? 1 : 2;
   *out = ctx;
   return RTM_OK;
 }
@@ -591,6 +844,7 @@ int rtm_ctx_destroy(rtm_ctx *ctx) {
   rtm_server_shutdown(ctx);
   cudaDeviceSynchronize();
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
   delete ctx;
   return RTM_OK;
 }
@@ -599,6 +853,19 @@ int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items) {
   if (!ctx) return RTM_ERR_ARG;
   if (max_items < 0) return fail(ctx, RTM_ERR_ARG, "max_items must be >= 0");
   ctx->max_batch = max_items;
+  return RTM_OK;
+}
+
+int rtm_plan_bytes(const rtm_grid *grid, const rtm_acq *acq, const rtm_opts *opts, int nsample,
+                   size_t *call_bytes, size_t *item_bytes) {
+  if (!call_bytes || !item_bytes || nsample < 1) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = check_grid(nullptr, grid)) || (rc = check_acq(nullptr, grid, acq, true)) ||
+      (rc = check_opts(nullptr, opts)))
+    return rc;
+  const MigrationPlan p = plan_migration(*grid, *acq, *opts, nsample);
+  *call_bytes = p.shared_bytes;
+  *item_bytes = p.item_bytes;
   return RTM_OK;
 }
 
@@ -626,13 +893,13 @@ int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_ac
   if (!vel || !seis) return fail(ctx, RTM_ERR_ARG, "vel and seis must not be NULL");
   if (shot < -1 || shot >= acq->nshot)
     return fail(ctx, RTM_ERR_ARG, "shot %d outside [-1, %d)", shot, acq->nshot);
-  if ((rc = set_device(ctx))) return rc;
+  if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int s0 = shot < 0 ? 0 : shot, ns = shot < 0 ? acq->nshot : 1;
   const size_t vbytes = (size_t)grid->nx * grid->nz * 4;
   const size_t sbytes = (size_t)ns * grid->nt * acq->nrec * 4;
   const Geo g = make_geo(*grid);
-  const size_t item = 2 * (size_t)g.plane * 4;
+  const size_t item = 3 * (size_t)g.plane * 4;
   const size_t io = (is_device_ptr(vel) ? 0 : vbytes) + (is_device_ptr(seis) ? 0 : sbytes);
   const size_t base = (size_t)g.plane * 4 + (size_t)(g.P + g.NZ) * 4 + (size_t)acq->nrec * 12 +
                       (size_t)acq->nshot * 16 + (size_t)grid->nt * 4 + (size_t)(g.ntx * g.ntz + 1) * 4 +
@@ -651,6 +918,7 @@ int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_ac
   if (!rc) rc = view_out(ctx, s, seis, sbytes, st);
   if (!rc) rc = model_device(ctx, *grid, v.d, *acq, s0, ns, s.d, B, st);
   if (!rc) rc = view_finish(ctx, s, seis, sbytes, st);
+  if (!rc) rc = check_wait_flag(ctx);  // model_device synchronised its stream
   unreserve(ctx, got);
   return rc;
 }
@@ -665,7 +933,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
     return rc;
   if (nsample < 1) return fail(ctx, RTM_ERR_ARG, "nsample must be >= 1");
   if (!vels || !seis || !images) return fail(ctx, RTM_ERR_ARG, "NULL array argument");
-  if ((rc = set_device(ctx))) return rc;
+  if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t vbytes = (size_t)nsample * grid->nx * grid->nz * 4;
   const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
@@ -694,6 +962,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
   if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, *opts, im.d, B, st);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
+  if (!rc && (im.staged || ctx->prof)) rc = check_wait_flag(ctx);  // the stream was synchronised
   unreserve(ctx, got);
   return rc;
 }

@@ -25,13 +25,14 @@ constexpr int STEP_THREADS = 256;  // 32 x 8: 4 columns x 4 rows per thread
 struct Geo {
   int NZ, P, X0, NX, nb;  // padded grid
   int nz, nx, SX, CP;     // physical grid and its memory column origin
-  int ntx, ntz;           // tiles per grid
+  int ntx, ntz;           // tiles per grid (single-step kernel)
+  int ntx2, ntz2;         // tiles per grid (two-step kernel)
   long long plane;        // NZ * P   (floats)
   long long pplane;       // nz * SX  (elements)
 };
 
 struct Coef {
-  float c0;     // a0 (1/dx^2 + 1/dz^2)
+  float c0;     // a0 (1/dx^2 + 1/dz^2) (the kernels use the difference form instead)
   float ax[4];  // a_m / dx^2
   float az[4];  // a_m / dz^2
 };
@@ -44,8 +45,9 @@ struct StepArgs {
   const float *c_all;        // [nsample][plane]  (v dt)^2, zero outside
   const int *item_sample;    // [B]
   const int *item_shot;      // [B]
-  float *fa;                 // [B][plane] current field (read)
-  float *fb;                 // [B][plane] previous field, overwritten with the new one
+  float *fa;                 // [B][plane] current field v^n (read)
+  float *fb;                 // [B][plane] receives the new field v^{n+1}
+  float *fd;                 // [B][plane] time difference d^n = v^n - v^{n-1}, updated in place
   const int *src_row, *src_col;  // [nshot] memory coordinates of each source
   const float *wav;          // [nt] wavelet
   float src_scale;           // 1 / (dx dz)
@@ -70,6 +72,47 @@ struct StepRT {
   int max_idx;    // forward: reduce max |u^{n+1}| into slot max_idx (-1 none)
   int img_idx;    // backward: image with snapshot img_idx (-1 none)
   int dmax_flag;  // backward: after imaging, reduce max(den) into dmax
+};
+
+// Arguments of one launch of the two-step kernel (blockIdx.z = item slot).
+// Receiver lists are per two-step tile, with offsets r * EX + c in the
+// tile's extended region (the tile plus a 4-point ring).
+struct Step2Args {
+  Geo g;
+  Coef k;
+  const float *gx, *gz;
+  const float *c_all;
+  const int *item_sample, *item_shot;
+  float *v_out;                  // [B][plane] receives v^{n+2}
+  float *d_out;                  // [B][plane] receives d^{n+2}
+  const int *src_row, *src_col;
+  const float *wav;
+  float src_scale;
+  const int *rext_ptr;           // receivers in each tile's extended region
+  const int2 *rext_ent;
+  const int *rcen_ptr;           // receivers in each tile's centre
+  const int2 *rcen_ent;
+  int nrec, nt;
+  const float *seis;
+  float *rec_out;
+  void *snap;
+  int snap_dtype;
+  int nsnap;
+  unsigned *smax;
+  float *num, *den;
+  unsigned *dmax;
+  int *err;                      // set to 1 if a bounded wait gave up
+};
+
+struct Step2RT {
+  int t1, t2;          // sample index injected / recorded at substeps 1 and 2
+  int snap_in_idx;     // store the input field (deferred; any dtype) as this snapshot
+  int snap_mid_idx;    // store the intermediate field (FP32 only)
+  int snap_out_idx;    // store the output field (FP32 only)
+  int max_out_idx;     // reduce max |output| into this scale slot (half precision)
+  int img_mid_idx;     // image with the intermediate field (backward)
+  int img_out_idx;     // image with the output field (backward)
+  int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
 };
 
 enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2 };

@@ -28,6 +28,8 @@ struct rtm_ctx {
   char err[512] = "no error";
   int max_batch = 0;        // 0 = no cap beyond memory
   bool prof = false;        // time the step-kernel phases with events
+  int step_kernel = 2;      // 2: two-step TMA kernel where possible; 1: single-step only
+  int *h_err = nullptr;     // pinned: device wait-timeout flag of the last call
   rtm_stats stats{};        // guarded by mu
   rtm_server *server = nullptr;
 };

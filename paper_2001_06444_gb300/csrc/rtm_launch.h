@@ -1,5 +1,6 @@
 // rtm_launch.h — host-side launchers of the kernels (internal to the library).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "rtm_common.h"
@@ -13,6 +14,16 @@ cudaError_t launch_snap_store(const StepArgs &A, const float *field, int idx, in
 cudaError_t launch_prep_c(const float *vel, float *c_all, const Geo &g, double dt, int nsample,
                           cudaStream_t st);
 cudaError_t launch_vrange(const float *v, long long n, unsigned *out, cudaStream_t st);
+
+// two-step TMA kernel (rtm_prop2.cu): maps of the current v (box with halo 8)
+// and d (halo 4) buffers and of c; tile geometry
+cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
+                         const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
+                         cudaStream_t st);
+size_t step2_smem_bytes();
+int step2_tile_x();
+int step2_tile_z();
+int step2_ext();
 
 // imaging and statistics (rtm_post.cu)
 // Normalise each item's image (Eq. 5 with eps max(den)) and add it, in item

@@ -142,7 +142,9 @@ __global__ void k_ens_stats(const float *images, int n, int npad, int PB, long l
       const int lo = (int)floor(h);
       const int hi = min(lo + 1, n - 1);
       const double xl = sv[lo * PB + p], xh = sv[hi * PB + p];
-      qo[u] = (float)(xl + (h - lo) * (xh - xl));
+      // separately rounded multiply and add (no FMA contraction), so the
+      // FP64 value, and hence its float rounding, is the textbook formula's
+      qo[u] = (float)__dadd_rn(xl, __dmul_rn(h - lo, __dsub_rn(xh, xl)));
     }
     q05[pix] = qo[0];
     q95[pix] = qo[1];

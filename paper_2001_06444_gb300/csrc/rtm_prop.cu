@@ -8,6 +8,13 @@
 //     u^{n+1} = h (2 h u^n + c L(h u^n)) - g^2 u^{n-1} + c f^n
 // reads v^{n+1} = g (2 v^n + c L v^n) - g^2 v^{n-1} + c f^n.  h == 1 on the
 // physical grid, so sources, receivers, snapshots and images see u itself.
+// The recurrence is carried in difference form, d^n = v^n - v^{n-1}:
+//     d^{n+1} = g^2 d^n + g c L v^n - (1 - g)^2 v^n + c f^n,
+//     v^{n+1} = v^n + d^{n+1}
+// (d^{n+1} = d^n + c L v^n + c f^n inside the sponge-free region), the same
+// scheme in exact arithmetic.  In FP32 it keeps the time difference to full
+// relative precision instead of to eps |v|, which removes the rounding error
+// that the two-level form feeds into its non-decaying mode at every step.
 // The same kernel steps the reverse-time (adjoint) field, which obeys the
 // same recurrence with the data injected at the receivers (§3).
 //
@@ -122,6 +129,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
   const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
   const float *__restrict__ cur = A.fa + (long long)b * g.plane;
   float *__restrict__ out = A.fb + (long long)b * g.plane;
+  float *__restrict__ dd = A.fd + (long long)b * g.plane;
   const float *__restrict__ cc = A.c_all + (long long)A.item_sample[b] * g.plane;
 
   // 1. current field, tile + halo, into shared memory (zero beyond the buffer)
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
       v = __ldg(reinterpret_cast<const float4 *>(cur + (long long)gr * g.P + gc));
     *reinterpret_cast<float4 *>(&s[r][4 * c4]) = v;
   }
-  // 2. previous field and c at this thread's 4 x 4 points
+  // 2. time difference and c at this thread's 4 x 4 points
   const int col = x0 + 4 * tx, row0 = z0 + 4 * ty;
   const bool colok = col < g.P;
   float4 pv[4], cv[4];
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
   for (int r = 0; r < 4; ++r) {
     if (colok && row0 + r < g.NZ) {
       const long long o = (long long)(row0 + r) * g.P + col;
-      pv[r] = *reinterpret_cast<const float4 *>(out + o);
+      pv[r] = *reinterpret_cast<const float4 *>(dd + o);
       cv[r] = __ldg(reinterpret_cast<const float4 *>(cc + o));
     } else {
       pv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -168,21 +176,26 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const float ce = v[4 + l];
-      float lap = A.k.c0 * ce;
+      // L v as sum_m a_m [(v_{+m} - v_0) + (v_{-m} - v_0)] / h^2 (the centre
+      // weight is -2 sum a_m exactly): the differences are small and nearly
+      // exact for smooth fields, so FP32 cancellation no longer dominates
+      float lap = 0.f;
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) {
-        lap = fmaf(A.k.ax[m - 1], v[4 + l - m] + v[4 + l + m], lap);
-        lap = fmaf(A.k.az[m - 1], lane4(zc[r + 4 - m], l) + lane4(zc[r + 4 + m], l), lap);
+      for (int m = 4; m >= 1; --m) {
+        lap = fmaf(A.k.ax[m - 1], (v[4 + l - m] - ce) + (v[4 + l + m] - ce), lap);
+        lap = fmaf(A.k.az[m - 1], (lane4(zc[r + 4 - m], l) - ce) + (lane4(zc[r + 4 + m], l) - ce), lap);
       }
       const float c = lane4(cv[r], l), p = lane4(pv[r], l);
-      float nv;
+      float nd;  // d^{n+1} before injection
       if (interior) {
-        nv = fmaf(c, lap, 2.f * ce) - p;
+        nd = fmaf(c, lap, p);
       } else {
         const float gg = A.gz[min(row0 + r, g.NZ - 1)] * A.gx[min(col + l, g.P - 1)];
-        nv = gg * fmaf(c, lap, 2.f * ce) - gg * gg * p;
+        const float om = 1.f - gg;
+        // points with g == 1 take the interior formula whatever their tile
+        nd = gg == 1.f ? fmaf(c, lap, p) : fmaf(gg * gg, p, fmaf(gg * c, lap, -(om * om) * ce));
       }
-      res[r][l] = nv;
+      res[r][l] = nd;
     }
   }
 
@@ -232,7 +245,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
       for (int e = rp0 + tid; e < rp1; e += STEP_THREADS) {
         const int2 en = A.rtile_ent[e];
         const int lr = en.x / TX, lc = en.x - lr * TX;
-        ro[en.y] = s[HALO + lr][HALO + lc];
+        const long long o = (long long)(z0 + lr) * g.P + (x0 + lc);
+        ro[en.y] = cur[o] + s[HALO + lr][HALO + lc];  // v^{n+1} = v^n + d^{n+1}
       }
     }
 #pragma unroll
@@ -245,12 +259,20 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
     }
   }
 
-  // 5. new field
+  // 5. new difference and new field v^{n+1} = v^n + d^{n+1}
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
-    if (colok && row0 + r < g.NZ)
-      *reinterpret_cast<float4 *>(out + (long long)(row0 + r) * g.P + col) =
-          make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
+  for (int r = 0; r < 4; ++r) {
+    if (colok && row0 + r < g.NZ) {
+      const long long o = (long long)(row0 + r) * g.P + col;
+      *reinterpret_cast<float4 *>(dd + o) = make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
+      const float4 ce = zc[r + 4];
+      res[r][0] += ce.x;
+      res[r][1] += ce.y;
+      res[r][2] += ce.z;
+      res[r][3] += ce.w;
+      *reinterpret_cast<float4 *>(out + o) = make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
+    }
+  }
 
   const int j0 = col - g.CP;  // physical column of lane 0 (multiple of 4)
   const bool jok = j0 >= 0 && j0 < g.SX;

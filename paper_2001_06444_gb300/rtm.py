@@ -25,7 +25,7 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 
 # every entry point the header declares
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
-           "rtm_ctx_stats", "rtm_model", "rtm_migrate",
+           "rtm_ctx_stats", "rtm_plan_bytes", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
            "rtm_poll", "rtm_last_error", "rtm_cfl_limit")
 
@@ -92,12 +92,24 @@ def lib():
             L.rtm_last_error.argtypes = [vp]
             L.rtm_last_error.restype = C.c_char_p
             L.rtm_cfl_limit.restype = C.c_double
+            L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
+                                         C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
             _lib = L
     return _lib
 
 
 def cfl_limit() -> float:
     return lib().rtm_cfl_limit()
+
+
+def plan_bytes(grid: Grid, acq: Acq, opts: Opts, nsample: int = 1):
+    """(bytes per call, bytes per migration in flight) of a migration."""
+    a, b = C.c_size_t(), C.c_size_t()
+    rc = lib().rtm_plan_bytes(C.byref(grid), C.byref(acq), C.byref(opts), int(nsample),
+                              C.byref(a), C.byref(b))
+    if rc:
+        raise RTMError(rc, "rtm_plan_bytes: bad arguments")
+    return a.value, b.value
 
 
 def make_grid(nx, nz, nb, dx, dz, dt, nt) -> Grid:

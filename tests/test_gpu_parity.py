@@ -155,6 +155,16 @@ def test_batch_size_does_not_change_the_image(ctx, flat):
     assert rel_l2(a, ora_migrate(s, s.vel, data, isnap=2)) <= IMG_TOL
 
 
+# Image error of the snapshot format itself (oracle with the quantisation
+# replayed vs exact snapshots, Laplacian-filtered flat-reflector image):
+# BF16 6.1e-3 / 1.20e-2 / 1.69e-2 and FP16 7.6e-4 / 1.5e-3 / 2.1e-3 at
+# isnap 1 / 4 / 8.  The filter amplifies the white quantisation noise ~14x,
+# so BF16's 8-bit significand cannot meet 1e-2 against exact snapshots at
+# isnap >= 4; FP16 with per-snapshot scaling can.
+EXACT_TOL = {(rtm.SNAP_F16, 1): 1e-2, (rtm.SNAP_F16, 4): 1e-2, (rtm.SNAP_F16, 8): 1e-2,
+             (rtm.SNAP_BF16, 1): 1e-2, (rtm.SNAP_BF16, 4): 1.5e-2, (rtm.SNAP_BF16, 8): 2e-2}
+
+
 @pytest.mark.parametrize("mode", [rtm.SNAP_BF16, rtm.SNAP_F16])
 @pytest.mark.parametrize("isnap", [1, 4, 8])
 def test_half_precision_snapshots(ctx, flat, mode, isnap):
@@ -163,7 +173,7 @@ def test_half_precision_snapshots(ctx, flat, mode, isnap):
     want_q = ora_migrate(s, s.vel, data[None], isnap=isnap, mode=mode)
     want_x = ora_migrate(s, s.vel, data[None], isnap=isnap, mode=0)
     assert rel_l2(got, want_q) <= HALF_IMG_TOL
-    assert rel_l2(got, want_x) <= HALF_IMG_TOL
+    assert rel_l2(got, want_x) <= EXACT_TOL[(mode, isnap)]
 
 
 def test_reciprocity_fp32(ctx):
@@ -292,3 +302,38 @@ def test_full_size_sampled_parity(ctx):
     gi = gpu_migrate(ctx, one, vm, data, isnap=4)
     oi = ora_migrate(one, vm, data, isnap=4)
     assert rel_l2(gi, oi) <= IMG_TOL
+
+
+def test_two_step_kernel_matches_single_step_bitwise(ctx):
+    """The two-step TMA kernel and the single-step kernel compute the same
+    per-point arithmetic in the same order, so modelling and migration agree
+    bit for bit (every snapshot format, even and odd isnap, odd nt, sponge
+    widths that are not multiples of 4)."""
+    import os
+
+    nx, nz, nt = 250, 90, 301
+    v = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=21, water_depth=80.0)
+    s = inputs.Survey(nx, nz, 13, 10.0, 10.0, 1e-3, nt, v, np.array([3, 120, 247], np.int32),
+                      np.array([1, 0, 2], np.int32), np.arange(nx, dtype=np.int32),
+                      np.full(nx, 1, np.int32), inputs.ricker(20.0, 1e-3, nt))
+    data = np.stack([ora_model(s, v, k) for k in range(3)])
+    vm = inputs.smooth(v, 10.0, 10.0, 30.0)
+    old = os.environ.get("RTM_STEP_KERNEL")
+    os.environ["RTM_STEP_KERNEL"] = "1"
+    try:
+        one = rtm.Context(0)
+    finally:
+        if old is None:
+            del os.environ["RTM_STEP_KERNEL"]
+        else:
+            os.environ["RTM_STEP_KERNEL"] = old
+    try:
+        for shot in range(3):
+            assert np.array_equal(gpu_model(one, s, v, shot), gpu_model(ctx, s, v, shot))
+        for isnap, mode in ((4, rtm.SNAP_F32), (3, rtm.SNAP_F32), (1, rtm.SNAP_F32),
+                            (4, rtm.SNAP_F16), (2, rtm.SNAP_BF16), (3, rtm.SNAP_F16)):
+            a = gpu_migrate(one, s, vm, data, isnap=isnap, dtype=mode)
+            b = gpu_migrate(ctx, s, vm, data, isnap=isnap, dtype=mode)
+            assert np.array_equal(a, b), (isnap, mode)
+    finally:
+        one.close()
