@@ -48,6 +48,11 @@ def parse():
     # smaller cases of the same workload, for profiler captures only
     p.add_argument("--shots", type=int, default=96)
     p.add_argument("--nt", type=int, default=5000)
+    # other workloads of the method, each printing its own JSON line
+    p.add_argument("--workload", default="migrate", choices=["migrate", "ensemble", "serve"])
+    p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
+    p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
+    p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
     return p.parse_args()
 
 
@@ -72,18 +77,20 @@ def measured_peaks():
 
 
 def profile_traffic():
-    """Per-update DRAM bytes of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+    """DRAM bytes per point update of the step kernels from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
     import hashlib
 
-    src = os.path.join(ROOT, "paper_2001_06444_gb300", "csrc", "rtm_prop.cu")
-    summ = os.path.join(ROOT, "profiles", "k_step_full_size.md")
+    h = hashlib.sha256()
+    for f in ("rtm_prop.cu", "rtm_prop2.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2001_06444_gb300", "csrc", f), "rb").read())
+    digest = h.hexdigest()[:16]
+    summ = os.path.join(ROOT, "profiles", "k_step2_small.md")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(summ):
             if line.startswith("traffic_bytes_per_update:"):
                 parts = line.split()
-                if len(parts) >= 4 and parts[3] == h:
+                if len(parts) >= 4 and parts[3] == digest:
                     return float(parts[1])
     except OSError:
         pass
@@ -290,11 +297,169 @@ def run_native(args, world, rank, local):
     ctx.close()
 
 
+def _survey_request(spec, snap, dev):
+    """A request of the mixed stream: data modelled once with the true model,
+    migrated with a 60 m smoothed one."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    s = inputs.scaled_survey(spec["nx"], spec["nz"], spec["nshot"], spec["nt"], spec["f"],
+                             spec["seed"])
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    vt = torch.from_numpy(s.vel.astype(np.float32)).to(dev)
+    vm = torch.from_numpy(inputs.smooth(s.vel, s.dx, s.dz, 60.0).astype(np.float32)).to(dev)
+    seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device=dev)
+    return dict(s=s, keep=keep, acq=acq, grid=grid, vt=vt, vm=vm, seis=seis, img=img,
+                opts=rtm.Opts(4, snap, 1e-6, 1))
+
+
+def run_serve(args, local):
+    """Poisson stream of mixed migration requests through rtm_submit/rtm_poll
+    (continuous batching, FP16 snapshots), against the plain form: the same
+    requests one after another, one shot per launch sequence, FP32 snapshots."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = rtm.Context(local)
+    specs = inputs.request_stream(args.requests, rate_hz=1.0)
+    reqs = [_survey_request(sp, rtm.SNAP_F16, dev) for sp in specs]
+    for r in reqs:
+        ctx.model(r["grid"], r["vt"], r["acq"], -1, r["seis"])
+    torch.cuda.synchronize()
+    total_shots = sum(r["s"].nshot for r in reqs)
+    # plain form: one request at a time, one shot in flight, FP32 snapshots
+    ctx.set_batch(1)
+    t = time.perf_counter()
+    for r in reqs:
+        ctx.migrate(r["grid"], r["vm"], r["acq"], r["seis"], rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1),
+                    r["img"])
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t
+    ctx.set_batch(0)
+    plain_img = [r["img"].clone() for r in reqs]
+
+    def serve(gaps_s):
+        """Submit request i after gaps_s[i] seconds; returns (wall, latencies)."""
+        for r in reqs:
+            r["img"].zero_()
+        torch.cuda.synchronize()
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for r, gap in zip(reqs, gaps_s):
+            due += gap
+            while time.perf_counter() < due:
+                time.sleep(0.0002)
+            sub = time.perf_counter()
+            req = rtm.Request(r["grid"], r["vm"].data_ptr(), r["acq"], r["seis"].data_ptr(),
+                              r["opts"], r["img"].data_ptr())
+            tickets.append((ctx.submit(req), sub))
+        done = {}
+        while len(done) < len(tickets):
+            for tk, sub in tickets:
+                if tk in done:
+                    continue
+                st, _ = ctx.poll(tk, 1)
+                if st in (rtm.REQ_DONE, rtm.REQ_FAILED):
+                    done[tk] = (st, time.perf_counter() - sub)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        failed = sum(1 for v in done.values() if v[0] != rtm.REQ_DONE)
+        return wall, np.array([done[tk][1] for tk, _ in tickets]), failed
+
+    # batched capacity: every request submitted at once
+    cap_wall, _, _ = serve(np.zeros(len(reqs)))
+    capacity = len(reqs) / cap_wall
+    rate = args.rate or 0.8 * capacity
+    unit_gaps = np.diff([0.0] + [sp["t"] for sp in specs])  # unit-rate Poisson gaps
+    served_s, lat, failed = serve(unit_gaps / rate)
+    errs = []
+    for r, p in zip(reqs, plain_img):
+        a, b = r["img"].double(), p.double()
+        errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
+    line = {
+        "workload": "serve_mixed_stream", "requests": len(reqs), "shots": total_shots,
+        "arrival_rate_per_s": rate, "snap_dtype": "f16",
+        "batched_capacity": {"shots_per_s": total_shots / cap_wall, "wall_s": cap_wall},
+        "served": {"shots_per_s": total_shots / served_s, "wall_s": served_s,
+                   "p50_latency_s": float(np.percentile(lat, 50)),
+                   "p99_latency_s": float(np.percentile(lat, 99)), "failed": failed},
+        "plain_fp32_one_shot": {"shots_per_s": total_shots / plain_s, "wall_s": plain_s},
+        "speedup_batched_vs_plain": plain_s / cap_wall,
+        "image_rel_l2_vs_plain_max": max(errs),
+        "grids": sorted({(sp["nx"], sp["nz"]) for sp in specs}),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_ensemble(args, local):
+    """All (sample, shot) migrations of a velocity ensemble in one call, then
+    the per-pixel statistics of the images."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = inputs.full_size(nshot=args.shots, nt=args.nt)
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    ens = inputs.ensemble(vm, s.dx, s.dz, args.samples)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    snap = {"f32": rtm.SNAP_F32, "bf16": rtm.SNAP_BF16, "f16": rtm.SNAP_F16}[args.snap]
+    ctx = rtm.Context(local)
+    vt = torch.from_numpy(s.vel.astype(np.float32)).to(dev)
+    seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
+    ctx.model(grid, vt, acq, -1, seis)
+    vels = torch.from_numpy(ens.astype(np.float32)).to(dev)
+    imgs = torch.empty((args.samples, s.nz, s.nx), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.stats(reset=True)
+    t = time.perf_counter()
+    ctx.migrate_ensemble(grid, vels, acq, seis, rtm.Opts(4, snap, 1e-6, 1), imgs)
+    torch.cuda.synchronize()
+    mig_s = time.perf_counter() - t
+    st = ctx.stats(reset=True)
+    npix = s.nz * s.nx
+    outs = [torch.empty(npix, dtype=tp, device=dev)
+            for tp in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    t = time.perf_counter()
+    ctx.ensemble_stats(imgs, *outs)
+    torch.cuda.synchronize()
+    stats_s = time.perf_counter() - t
+    peak, _ = measured_peaks()
+    achieved = st["step_bytes"] / (st["step_ms"] / 1e3) / 1e9
+    line = {
+        "workload": f"ensemble_{args.samples}x{s.nshot}_1701x351_nt{s.nt}_{args.snap}snap",
+        "migrations": args.samples * s.nshot, "migration_s": mig_s,
+        "shots_per_s": args.samples * s.nshot / mig_s,
+        "gpt_updates_per_s": st["point_updates"] / mig_s / 1e9,
+        "step_kernel_gbs": achieved, "frac_of_measured_hbm": achieved / peak,
+        "stats_ms": 1e3 * stats_s,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "serve":
+        run_serve(args, local)
+    elif args.workload == "ensemble":
+        run_ensemble(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:
