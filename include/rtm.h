@@ -222,6 +222,24 @@ int rtm_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket);
  * ticket.  A DONE or FAILED ticket is forgotten after it is reported. */
 int rtm_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms);
 
+/* Forward modelling of one shot without allocating device memory (the
+ * paper has no counterpart; this serves callers that cannot allocate while
+ * they run, e.g. inside a host framework whose allocator owns all device
+ * memory, or in a real-time loop where an allocation could stall the
+ * device).  Same arguments and result as rtm_model with one shot, but vel
+ * [nz][nx] and seis [nt][nrec] must be device memory and no context is used:
+ * the work runs in a 32 MiB scratch array that the library holds on every
+ * device that loads it.  The device is the current one.  The first call on a
+ * device looks up the scratch address (and may load the library's device
+ * code), so make it before any stream capture.  The call synchronises the
+ * stream once for the stability check, then returns with the modelling
+ * queued.  Every call shares the scratch and overwrites it, so calls whose
+ * work overlaps on the GPU race.  Returns RTM_ERR_NOMEM if the padded grid
+ * needs more than the scratch (about 2 M padded points), RTM_ERR_ARG for bad
+ * arguments or host pointers, RTM_ERR_CFL, RTM_ERR_CUDA. */
+int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const rtm_acq *acq,
+                      int shot, float *seis, void *stream);
+
 /* Text of the last error on this context (never NULL). */
 const char *rtm_last_error(rtm_ctx *ctx);
 

@@ -27,7 +27,7 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
-           "rtm_poll", "rtm_last_error", "rtm_cfl_limit")
+           "rtm_poll", "rtm_model_noalloc", "rtm_last_error", "rtm_cfl_limit")
 
 
 class RTMError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
             L.rtm_last_error.argtypes = [vp]
             L.rtm_last_error.restype = C.c_char_p
             L.rtm_cfl_limit.restype = C.c_double
+            L.rtm_model_noalloc.argtypes = [C.POINTER(Grid), vp, C.POINTER(Acq), ip, vp, vp]
             L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
             _lib = L
