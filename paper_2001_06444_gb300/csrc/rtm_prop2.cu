@@ -152,11 +152,19 @@ __device__ __forceinline__ void block_max_atomic(float v, unsigned *dst, float *
   }
 }
 
+// Paired FP32 arithmetic (two lanes per instruction).  Each lane rounds
+// exactly like the scalar operation, so results equal the scalar kernel's;
+// a - b is formed as fma(b, -1, a), which rounds once like a subtraction.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 // One leapfrog update of 4 consecutive points in difference form.
 //   zc[0..8]: the 9 rows (centre row zc[4]) of the 4-column strip,
 //   xl, xr:   the 4 columns left and right of the strip in the centre row,
 //   dv, cv:   d^n and c at the strip.
-// Returns d^{n+1} (before injection); v^{n+1} = v^n + d^{n+1}.
+// Returns d^{n+1} (before injection); v^{n+1} = v^n + d^{n+1}.  Lanes are
+// processed in pairs (0,1) and (2,3).
 __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, const float4 &xr,
                                           const float4 &dv, const float4 &cv, const Coef &k,
                                           bool interior, float gzr, const float *gx, int col,
@@ -165,26 +173,41 @@ __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, co
   const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
   float out[4];
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
-    const float ce = v[4 + l];
-    float lap = 0.f;
+  for (int l = 0; l < 4; l += 2) {
+    const float2 ce = make_float2(v[4 + l], v[5 + l]);
+    float2 lap = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 4; m >= 1; --m) {
-      lap = fmaf(k.ax[m - 1], (v[4 + l - m] - ce) + (v[4 + l + m] - ce), lap);
-      lap = fmaf(k.az[m - 1], (lane4(zc[4 - m], l) - ce) + (lane4(zc[4 + m], l) - ce), lap);
+      const float2 xm = make_float2(v[4 + l - m], v[5 + l - m]);
+      const float2 xp = make_float2(v[4 + l + m], v[5 + l + m]);
+      const float2 tx = __fadd2_rn(sub2(xm, ce), sub2(xp, ce));
+      lap = __ffma2_rn(make_float2(k.ax[m - 1], k.ax[m - 1]), tx, lap);
+      const float2 zm = l == 0 ? make_float2(zc[4 - m].x, zc[4 - m].y)
+                               : make_float2(zc[4 - m].z, zc[4 - m].w);
+      const float2 zp = l == 0 ? make_float2(zc[4 + m].x, zc[4 + m].y)
+                               : make_float2(zc[4 + m].z, zc[4 + m].w);
+      const float2 tz = __fadd2_rn(sub2(zm, ce), sub2(zp, ce));
+      lap = __ffma2_rn(make_float2(k.az[m - 1], k.az[m - 1]), tz, lap);
     }
-    const float c = lane4(cv, l), p = lane4(dv, l);
-    float nd;
+    const float2 c = l == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w);
+    const float2 p = l == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);
     if (interior) {
-      nd = fmaf(c, lap, p);
+      const float2 nd = __ffma2_rn(c, lap, p);
+      out[l] = nd.x;
+      out[l + 1] = nd.y;
     } else {
-      const int cc = min(max(col + l, 0), P - 1);
-      const float gg = gzr * gx[cc];
-      const float om = 1.f - gg;
-      // points with g == 1 take the interior formula whatever their tile
-      nd = gg == 1.f ? fmaf(c, lap, p) : fmaf(gg * gg, p, fmaf(gg * c, lap, -(om * om) * ce));
+      const float lp[2] = {lap.x, lap.y}, cc2[2] = {c.x, c.y}, pp[2] = {p.x, p.y},
+                  cce[2] = {ce.x, ce.y};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = min(max(col + l + h, 0), P - 1);
+        const float gg = gzr * gx[cc];
+        const float om = 1.f - gg;
+        // points with g == 1 take the interior formula whatever their tile
+        out[l + h] = gg == 1.f ? fmaf(cc2[h], lp[h], pp[h])
+                               : fmaf(gg * gg, pp[h], fmaf(gg * cc2[h], lp[h], -(om * om) * cce[h]));
+      }
     }
-    out[l] = nd;
   }
   return make_float4(out[0], out[1], out[2], out[3]);
 }
@@ -219,6 +242,32 @@ __global__ void __launch_bounds__(NTH, 3)
     tma_load_3d(&S.v0[0][0], &map_v, x0 - 8, z0 - 8, b, &S.bar);
     tma_load_3d(&S.d[0][0], &map_d, x0 - 4, z0 - 4, b, &S.bar);
     tma_load_3d(&S.c[0][0], &map_c, x0 - 4, z0 - 4, smp, &S.bar);
+  }
+  // backward imaging launches: start pulling this thread's num, den and
+  // snapshot rows into L2 while the tile loads and the stencil run
+  if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0) && tx < C2X / 4) {
+    const int j0 = x0 + 4 * tx - g.CP;
+    if (j0 >= 0 && j0 < g.SX) {
+      const int esz = A.snap_dtype == 0 ? 4 : 2;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int i = z0 + 3 * ty + r - g.nb;
+        if (i >= 0 && i < g.nz) {
+          const long long po = (long long)b * g.pplane + (long long)i * g.SX + j0;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A.num + po));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(A.den + po));
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int idx = u == 0 ? rt.img_mid_idx : rt.img_out_idx;
+            if (idx >= 0) {
+              const long long so = ((long long)b * A.nsnap + idx) * g.pplane + (long long)i * g.SX + j0;
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(A.snap) +
+                                                             so * esz));
+            }
+          }
+        }
+      }
+    }
   }
   {
     unsigned it = 0;
