@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--snap", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the mixed-stream latency run")
     # smaller cases of the same workload, for profiler captures only
     p.add_argument("--shots", type=int, default=96)
     p.add_argument("--nt", type=int, default=5000)
@@ -271,6 +272,23 @@ def run_native(args, world, rank, local):
                "sample": f"2 of the {s.nshot} shots, all {s.nt} steps (fwd+bwd+imaging, FP64), "
                          f"{dt:.1f} s"}
 
+    ctx.close()
+    serving = None
+    if world == 1 and not args.no_serve:
+        del seis, vel_true, vel_mig, image
+        torch.cuda.empty_cache()
+        sv = serve_measurement(local, 32)
+        serving = {"workload": "mixed stream: 32 Poisson requests, grids 201x101..2401x601, "
+                               "1-32 shots, 2000-6000 steps, FP16 snapshots",
+                   "p50_latency_s": sv["served"]["p50_latency_s"],
+                   "p99_latency_s": sv["served"]["p99_latency_s"],
+                   "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                   "served_shots_per_s": sv["served"]["shots_per_s"],
+                   "batched_capacity_shots_per_s": sv["batched_capacity"]["shots_per_s"],
+                   "plain_fp32_one_shot_shots_per_s": sv["plain_fp32_one_shot"]["shots_per_s"],
+                   "batched_vs_plain": sv["speedup_batched_vs_plain"],
+                   "image_rel_l2_vs_plain_max": sv["image_rel_l2_vs_plain_max"]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world,
@@ -286,15 +304,15 @@ def run_native(args, world, rank, local):
             "gpt_updates_per_s": gpt,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "kernel": "k_step (forward+backward phases)",
+                         "kernel": "k_step2 (two-step TMA kernel; forward+backward phases)",
                          "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": stats["step_bytes"] / max(1, launches_step),
                          "avg_launch_us": 1e3 * stats["step_ms"] / max(1, launches_step)},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
             "gpu_launches": int(stats["launches"]),
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def _survey_request(spec, snap, dev):
@@ -317,10 +335,11 @@ def _survey_request(spec, snap, dev):
                 opts=rtm.Opts(4, snap, 1e-6, 1))
 
 
-def run_serve(args, local):
+def serve_measurement(local, nreq, rate_arg=0.0):
     """Poisson stream of mixed migration requests through rtm_submit/rtm_poll
     (continuous batching, FP16 snapshots), against the plain form: the same
-    requests one after another, one shot per launch sequence, FP32 snapshots."""
+    requests one after another, one shot per launch sequence, FP32 snapshots.
+    Returns a dict; the stream is the seeded one of inputs.request_stream."""
     import torch
 
     from paper_2001_06444_gb300 import inputs, rtm
@@ -328,7 +347,7 @@ def run_serve(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = rtm.Context(local)
-    specs = inputs.request_stream(args.requests, rate_hz=1.0)
+    specs = inputs.request_stream(nreq, rate_hz=1.0)
     reqs = [_survey_request(sp, rtm.SNAP_F16, dev) for sp in specs]
     for r in reqs:
         ctx.model(r["grid"], r["vt"], r["acq"], -1, r["seis"])
@@ -377,7 +396,7 @@ def run_serve(args, local):
     # batched capacity: every request submitted at once
     cap_wall, _, _ = serve(np.zeros(len(reqs)))
     capacity = len(reqs) / cap_wall
-    rate = args.rate or 0.8 * capacity
+    rate = rate_arg or 0.8 * capacity
     unit_gaps = np.diff([0.0] + [sp["t"] for sp in specs])  # unit-rate Poisson gaps
     served_s, lat, failed = serve(unit_gaps / rate)
     errs = []
@@ -396,8 +415,14 @@ def run_serve(args, local):
         "image_rel_l2_vs_plain_max": max(errs),
         "grids": sorted({(sp["nx"], sp["nz"]) for sp in specs}),
     }
-    print(json.dumps(line), flush=True)
     ctx.close()
+    del reqs
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_serve(args, local):
+    print(json.dumps(serve_measurement(local, args.requests, args.rate)), flush=True)
 
 
 def run_ensemble(args, local):
