@@ -213,6 +213,7 @@ def run_native(args, world, rank, local):
     torch.cuda.synchronize()
     if args.batch:
         ctx.set_batch(args.batch)
+    tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
     for _ in range(args.warmup):
         ctx.migrate(grid, vel_mig, acq, seis, opts, image)
     torch.cuda.synchronize()
@@ -225,10 +226,12 @@ def run_native(args, world, rank, local):
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
     e0.record(st)
     for _ in range(args.steps):
         ctx.migrate(grid, vel_mig, acq, seis, opts, image)
     e1.record(st)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
     ck = clocks.stop()
@@ -299,6 +302,7 @@ def run_native(args, world, rank, local):
                        else f"rtm_1701x351_{s.nshot}shots_nt{s.nt}_isnap4_{args.snap}snap", "grid": "1701x351 +20 sponge, 10 m", "shots": s.nshot,
                        "nt": s.nt, "isnap": 4, "snap_dtype": args.snap,
                        "items_in_flight": args.batch or "memory budget",
+                       "launch_config": tuned,
                        "l2": "inputs larger than L2 (3.0 GB snapshot store per shot)",
                        "parallelism": f"weak x{world}, independent migrations per GPU"},
             "gpt_updates_per_s": gpt,

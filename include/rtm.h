@@ -147,6 +147,20 @@ int rtm_ctx_set_profiling(rtm_ctx *ctx, int on);
 /* Copy the counters into *out; reset them if reset != 0. */
 int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset);
 
+/* Choose how migrations shaped like (grid, acq, opts) are launched on this
+ * context, by timing short trial migrations (trial_steps time steps, 64 if
+ * <= 0) of every candidate on synthetic inputs: time-block depth (the
+ * two-step kernel, which advances each grid two steps per launch with a
+ * 120 x 24 tile plus a 4-point ring, or the single-step kernel), the number
+ * of migrations in flight, and whether each phase of a batch is captured
+ * and replayed as a CUDA graph.  The fastest is used by later rtm_migrate,
+ * rtm_migrate_ensemble and request-loop calls with the same grid, nt, isnap
+ * and snapshot format.  All candidates give bit-identical results.
+ * choice (nullable, 3 ints): {step kernel 1 or 2, items cap (0 = memory),
+ * graph 0 or 1}.  Synchronises the stream. */
+int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq,
+                 const rtm_opts *opts, int trial_steps, int *choice, void *stream);
+
 /* Forward modelling (§2.2, Eq. 4 with the wavelet as source term; Listing 1,
  * `isotropicAcousticModeling`).  vel: [nz][nx] m/s; shot: index into acq, or
  * -1 for every shot of acq (advanced side by side); seis: output

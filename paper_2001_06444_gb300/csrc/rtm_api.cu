@@ -322,7 +322,7 @@ static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<i
 
 // Upload the per-call tables shared by all items.
 static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
-                        int nsample, const float *vel_d, cudaStream_t st) {
+                        int nsample, const float *vel_d, cudaStream_t st, int step_kernel) {
   C.g = make_geo(gr);
   C.k = make_coef(gr);
   const Geo &g = C.g;
@@ -387,7 +387,7 @@ static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_a
   CU(cudaMemcpyAsync(C.wav.p, acq.wavelet, (size_t)gr.nt * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(C.err.p, 0, 16, st));
   CU(launch_prep_c(vel_d, C.c_all.as<float>(), g, gr.dt, nsample, st));
-  if (ctx->step_kernel == 2) {
+  if (step_kernel == 2) {
     const int H = step2_ext();
     int rc = make_map(ctx, &C.mc, C.c_all.as<float>(), g, nsample, step2_tile_x() + 2 * H,
                       step2_tile_z() + 2 * H);
@@ -407,11 +407,12 @@ struct Fields {
   int cv = 0, cd = 0;  // index of the current v and d buffer
 };
 
-static int alloc_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int B, cudaStream_t st) {
+static int alloc_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int B, cudaStream_t st,
+                        int step_kernel) {
   for (int i = 0; i < 2; ++i) {
     CU(F.v[i].alloc(ctx, (size_t)B * g.plane * 4, st));
     CU(F.d[i].alloc(ctx, (size_t)B * g.plane * 4, st));
-    if (ctx->step_kernel == 2) {
+    if (step_kernel == 2) {
       const int H = step2_ext();
       int rc = make_map(ctx, &F.mv[i], F.v[i].as<float>(), g, B, step2_tile_x() + 4 * H,
                         step2_tile_z() + 4 * H);
@@ -503,11 +504,42 @@ static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields 
   return RTM_OK;
 }
 
+RunConfig config_for(rtm_ctx *ctx, const rtm_grid &gr, const rtm_opts &op) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->tuned.find(TuneKey{gr.nx, gr.nz, gr.nb, gr.nt, op.isnap, op.snap_dtype});
+  return it != ctx->tuned.end() ? it->second : ctx->defaults;
+}
+
+// Issue `issue()` on st, either directly or captured once into a CUDA graph
+// that is then launched (one launch for a whole phase of a batch).
+template <class F>
+static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
+  // the legacy default stream cannot be captured: launch directly there
+  if (!graph || st == nullptr || st == cudaStreamLegacy) return issue();
+  CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = issue();
+  cudaGraph_t gph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &gph);
+  if (rc) {
+    if (gph) cudaGraphDestroy(gph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, gph, 0);
+  cudaGraphDestroy(gph);
+  if (ei != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+  const cudaError_t el = cudaGraphLaunch(ex, st);
+  cudaGraphExecDestroy(ex);  // released once the launch completes
+  if (el != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(el));
+  return RTM_OK;
+}
+
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
-                   int B, cudaStream_t st) {
+                   int B, cudaStream_t st, const RunConfig &cfg) {
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st);
+  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel);
   if (rc) return rc;
   const Geo &g = C.g;
   const int nsnap = gr.nt / op.isnap;
@@ -523,7 +555,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   CU(C.items.alloc(ctx, items.size() * 4, st));
   CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
   Fields F;
-  if ((rc = alloc_fields(ctx, F, g, B, st))) return rc;
+  if ((rc = alloc_fields(ctx, F, g, B, st, cfg.step_kernel))) return rc;
   DevBuf snap, smax, num, den, dmax, stack, comp;
   const size_t esz = snap_elem_bytes(op.snap_dtype);
   CU(snap.alloc(ctx, std::max<size_t>((size_t)B * nsnap * g.pplane * esz, 16), st));
@@ -566,7 +598,8 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   A.dmax = dmax.as<unsigned>();
   const int isnap = op.isnap, nt = gr.nt;
   const bool half = op.snap_dtype != RTM_SNAP_F32;
-  const bool two = ctx->step_kernel == 2;
+  const bool two = cfg.step_kernel == 2;
+  const bool graph = cfg.graph != 0;
   auto inK = [&](int m) { return m >= 1 && m <= nt && m % isnap == 0; };
   for (long long q0 = 0; q0 < nitems; q0 += B) {
     const int nb = (int)std::min<long long>(B, nitems - q0);
@@ -580,33 +613,40 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     // forward: snapshots S^k, k in K
     if ((rc = mark())) return rc;
     bool stored = false;  // the current field, if in K, is already stored
-    for (int n = 0; n < nt;) {
-      if (two && n + 2 <= nt && (!half || isnap % 2 == 0)) {
-        Step2RT r;
-        r.t1 = n;
-        r.t2 = n + 1;
-        r.snap_in_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
-        r.snap_mid_idx = (!half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
-        r.snap_out_idx = (!half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
-        r.max_out_idx = (half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
-        r.img_mid_idx = r.img_out_idx = -1;
-        r.dmax_flag = 0;
-        if ((rc = step2(ctx, MODE_FWD, A2, C, F, r, nb, st))) return rc;
-        stored = !half;
-        n += 2;
-      } else {
-        StepRT r{};
-        r.n = n;
-        r.snap_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
-        r.max_idx = (half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
-        r.img_idx = -1;
-        r.dmax_flag = 0;
-        if ((rc = step1(ctx, MODE_FWD, A, F, r, nb, st))) return rc;
-        stored = false;
-        n += 1;
+    long long nlaunch = 0;
+    rc = run_phase(ctx, graph, st, [&]() -> int {
+      int r2;
+      for (int n = 0; n < nt;) {
+        if (two && n + 2 <= nt && (!half || isnap % 2 == 0)) {
+          Step2RT r;
+          r.t1 = n;
+          r.t2 = n + 1;
+          r.snap_in_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
+          r.snap_mid_idx = (!half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
+          r.snap_out_idx = (!half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
+          r.max_out_idx = (half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
+          r.img_mid_idx = r.img_out_idx = -1;
+          r.dmax_flag = 0;
+          if ((r2 = step2(ctx, MODE_FWD, A2, C, F, r, nb, st))) return r2;
+          stored = !half;
+          n += 2;
+        } else {
+          StepRT r{};
+          r.n = n;
+          r.snap_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
+          r.max_idx = (half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
+          r.img_idx = -1;
+          r.dmax_flag = 0;
+          if ((r2 = step1(ctx, MODE_FWD, A, F, r, nb, st))) return r2;
+          stored = false;
+          n += 1;
+        }
+        ++nlaunch;
       }
-      ++step_launches;
-    }
+      return RTM_OK;
+    });
+    if (rc) return rc;
+    step_launches += nlaunch;
     if ((rc = mark())) return rc;
     if (inK(nt) && !stored) {
       CU(launch_snap_store(A, F.v[F.cv].as<float>(), nt / isnap - 1, nb, st));
@@ -615,28 +655,35 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     // backward: receiver wavefield and imaging
     if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
     if ((rc = mark())) return rc;
-    for (int k = nt; k >= 1;) {
-      if (two && k >= 2) {
-        Step2RT r;
-        r.t1 = k - 1;
-        r.t2 = k - 2;
-        r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
-        r.img_mid_idx = inK(k) ? k / isnap - 1 : -1;
-        r.img_out_idx = inK(k - 1) ? (k - 1) / isnap - 1 : -1;
-        r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
-        if ((rc = step2(ctx, MODE_BWD, A2, C, F, r, nb, st))) return rc;
-        k -= 2;
-      } else {
-        StepRT r{};
-        r.n = k;
-        r.snap_idx = r.max_idx = -1;
-        r.img_idx = inK(k) ? k / isnap - 1 : -1;
-        r.dmax_flag = (k == isnap) ? 1 : 0;
-        if ((rc = step1(ctx, MODE_BWD, A, F, r, nb, st))) return rc;
-        k -= 1;
+    nlaunch = 0;
+    rc = run_phase(ctx, graph, st, [&]() -> int {
+      int r2;
+      for (int k = nt; k >= 1;) {
+        if (two && k >= 2) {
+          Step2RT r;
+          r.t1 = k - 1;
+          r.t2 = k - 2;
+          r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+          r.img_mid_idx = inK(k) ? k / isnap - 1 : -1;
+          r.img_out_idx = inK(k - 1) ? (k - 1) / isnap - 1 : -1;
+          r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
+          if ((r2 = step2(ctx, MODE_BWD, A2, C, F, r, nb, st))) return r2;
+          k -= 2;
+        } else {
+          StepRT r{};
+          r.n = k;
+          r.snap_idx = r.max_idx = -1;
+          r.img_idx = inK(k) ? k / isnap - 1 : -1;
+          r.dmax_flag = (k == isnap) ? 1 : 0;
+          if ((r2 = step1(ctx, MODE_BWD, A, F, r, nb, st))) return r2;
+          k -= 1;
+        }
+        ++nlaunch;
       }
-      ++step_launches;
-    }
+      return RTM_OK;
+    });
+    if (rc) return rc;
+    step_launches += nlaunch;
     if ((rc = mark())) return rc;
     CU(launch_norm_stack(A.num, A.den, A.dmax, A.item_sample, nb, (float)op.eps, g.pplane,
                          stack.as<float>(), comp.as<float>(), st));
@@ -677,8 +724,9 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
 static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
                         const rtm_acq &acq, int s0, int ns, float *seis_d, int B,
                         cudaStream_t st) {
+  const int sk = ctx->defaults.step_kernel;
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st);
+  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk);
   if (rc) return rc;
   const Geo &g = C.g;
   if (B > ns) B = ns;
@@ -691,10 +739,10 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
   CU(C.items.alloc(ctx, items.size() * 4, st));
   CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
   Fields F;
-  if ((rc = alloc_fields(ctx, F, g, B, st))) return rc;
+  if ((rc = alloc_fields(ctx, F, g, B, st, sk))) return rc;
   StepArgs A;
   fill_args(A, C, gr, acq);
-  const bool two = ctx->step_kernel == 2;
+  const bool two = sk == 2;
   long long launches = 0;
   for (int q0 = 0; q0 < ns; q0 += B) {
     const int nb = std::min(B, ns - q0);
@@ -833,7 +881,10 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
   *ctx->h_err = 0;
   // RTM_STEP_KERNEL=1 restricts propagation to the single-step kernel
   const char *sk = std::getenv("RTM_STEP_KERNEL");
-  ctx->step_kernel = (sk && sk[0] == '1') ? 1 : 2;
+  ctx->defaults.step_kernel = (sk && sk[0] == '1') ? 1 : 2;
+  // RTM_GRAPHS=1 captures each phase of a batch in a CUDA graph by default
+  const char *gr = std::getenv("RTM_GRAPHS");
+  ctx->defaults.graph = (gr && gr[0] == '1') ? 1 : 0;
   *out = ctx;
   return RTM_OK;
 }
@@ -853,6 +904,123 @@ int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items) {
   if (!ctx) return RTM_ERR_ARG;
   if (max_items < 0) return fail(ctx, RTM_ERR_ARG, "max_items must be >= 0");
   ctx->max_batch = max_items;
+  return RTM_OK;
+}
+
+int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const rtm_opts *opts,
+                 int trial_steps, int *choice, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true)) ||
+      (rc = check_opts(ctx, opts)))
+    return rc;
+  if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
+  // trials run on a private stream (capturable), after the caller's work
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return fail(ctx, RTM_ERR_CUDA, "could not synchronise the caller's stream");
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(ctx, RTM_ERR_CUDA, "could not create a stream for the trials");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  };
+  StreamGuard guard{st};
+  // trial: the same grid and acquisition over fewer steps, synthetic inputs
+  rtm_grid tg = *grid;
+  tg.nt = trial_steps > 0 ? trial_steps : 64;
+  tg.nt = std::max(2, std::min(tg.nt, grid->nt));
+  rtm_opts to = *opts;
+  const long long nitems = acq->nshot;
+  const MigrationPlan plan = plan_migration(tg, *acq, to, 1);
+  const size_t vbytes = (size_t)grid->nx * grid->nz * 4;
+  const size_t sbytes = (size_t)acq->nshot * tg.nt * acq->nrec * 4;
+  const size_t io = 2 * vbytes + sbytes;
+  const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
+  const size_t want = plan.shared_bytes + io + (size_t)nitems * plan.item_bytes;
+  if (need1 > ctx->budget) return fail(ctx, RTM_ERR_NOMEM, "trial does not fit the budget");
+  const size_t got = reserve_wait(ctx, want, need1, 600000);
+  if (!got) return fail(ctx, RTM_ERR_TIMEOUT, "waited 600 s for device memory");
+  const long long bmax = std::max<long long>(
+      1, std::min<long long>(nitems, (long long)((got - plan.shared_bytes - io) / plan.item_bytes)));
+  DevBuf vel, seis, img;
+  int best = -1;
+  double best_t = 1e300;
+  std::vector<RunConfig> cand;
+  for (int sk : {2, 1})
+    for (int graph : {0, 1})
+      for (long long items : {bmax, (bmax + 1) / 2}) {
+        RunConfig c;
+        c.step_kernel = sk;
+        c.graph = graph;
+        c.max_items = items >= nitems ? 0 : (int)items;
+        bool dup = false;
+        for (auto &o : cand)
+          dup |= o.step_kernel == c.step_kernel && o.graph == c.graph && o.max_items == c.max_items;
+        if (!dup) cand.push_back(c);
+      }
+  rc = RTM_OK;
+  do {
+    if ((rc = vel.alloc(ctx, vbytes, st)) || (rc = seis.alloc(ctx, sbytes, st)) ||
+        (rc = img.alloc(ctx, vbytes, st))) {
+      rc = fail(ctx, RTM_ERR_CUDA, "trial buffers");
+      break;
+    }
+    // constant velocity at half the stability limit; zero data
+    const double vt = 0.5 * 2.0 /
+                      (grid->dt * std::sqrt((1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dz * grid->dz)) *
+                                            2048.0 / 315.0));
+    std::vector<float> hv((size_t)grid->nx * grid->nz, (float)vt);
+    if (cudaMemcpyAsync(vel.p, hv.data(), vbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(seis.p, 0, sbytes, st) != cudaSuccess) {
+      rc = fail(ctx, RTM_ERR_CUDA, "trial inputs");
+      break;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (size_t i = 0; i < cand.size() && !rc; ++i) {
+      const RunConfig &c = cand[i];
+      const long long cap = c.max_items > 0 ? c.max_items : bmax;
+      const long long nbatch = (nitems + cap - 1) / cap;
+      const int B = (int)((nitems + nbatch - 1) / nbatch);
+      float ms = 0.f, best_ms = 1e30f;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {  // first run warms up
+        cudaEventRecord(e0, st);
+        rc = migrate_device(ctx, tg, 1, vel.as<float>(), *acq, seis.as<float>(), to,
+                            img.as<float>(), B, st, c);
+        cudaEventRecord(e1, st);
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, RTM_ERR_CUDA, "trial sync");
+        if (!rc && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+          best_ms = std::min(best_ms, ms);
+      }
+      if (!rc && best_ms < best_t) {
+        best_t = best_ms;
+        best = (int)i;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  } while (0);
+  vel.release();
+  seis.release();
+  img.release();
+  if (!rc) rc = check_wait_flag(ctx);
+  if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(ctx, RTM_ERR_CUDA, "sync");
+  unreserve(ctx, got);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned[TuneKey{grid->nx, grid->nz, grid->nb, grid->nt, opts->isnap, opts->snap_dtype}] = cand[best];
+  }
+  if (choice) {
+    choice[0] = cand[best].step_kernel;
+    choice[1] = cand[best].max_items;
+    choice[2] = cand[best].graph;
+  }
   return RTM_OK;
 }
 
@@ -942,9 +1110,10 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
                     (is_device_ptr(images) ? 0 : vbytes);
   const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
   const long long nitems = (long long)nsample * acq->nshot;
+  const RunConfig cfg = config_for(ctx, *grid, *opts);
   size_t want = plan.shared_bytes + io + (size_t)nitems * plan.item_bytes;
-  if (ctx->max_batch > 0)
-    want = std::min(want, plan.shared_bytes + io + (size_t)ctx->max_batch * plan.item_bytes);
+  const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
+  if (cap > 0) want = std::min(want, plan.shared_bytes + io + (size_t)cap * plan.item_bytes);
   if (need1 > ctx->budget)
     return fail(ctx, RTM_ERR_NOMEM, "one migration needs %.3f GB, budget is %.3f GB",
                 need1 / 1e9, ctx->budget / 1e9);
@@ -960,7 +1129,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
   if (!rc) rc = view_in(ctx, s, seis, sbytes, st);
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
-  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, *opts, im.d, B, st);
+  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, *opts, im.d, B, st, cfg);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
   if (!rc && (im.staged || ctx->prof)) rc = check_wait_flag(ctx);  // the stream was synchronised
   unreserve(ctx, got);

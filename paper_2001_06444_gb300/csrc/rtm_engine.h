@@ -18,6 +18,25 @@
 
 struct rtm_server;
 
+namespace rtm {
+// How a migration is launched (all choices give bit-identical results).
+struct RunConfig {
+  int step_kernel = 2;  // 2: two-step TMA kernel where possible; 1: single-step only
+  int max_items = 0;    // cap on items in flight (0 = memory budget)
+  int graph = 0;        // 1: capture each phase of a batch in a CUDA graph
+};
+// Shape key of the autotuner cache.
+struct TuneKey {
+  int nx, nz, nb, nt, isnap, dtype;
+  bool operator<(const TuneKey &o) const {
+    const int a[6] = {nx, nz, nb, nt, isnap, dtype}, b[6] = {o.nx, o.nz, o.nb, o.nt, o.isnap, o.dtype};
+    for (int i = 0; i < 6; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+}  // namespace rtm
+
 struct rtm_ctx {
   int device = 0;
   size_t budget = 0;        // bytes of device memory the context may hold
@@ -28,7 +47,8 @@ struct rtm_ctx {
   char err[512] = "no error";
   int max_batch = 0;        // 0 = no cap beyond memory
   bool prof = false;        // time the step-kernel phases with events
-  int step_kernel = 2;      // 2: two-step TMA kernel where possible; 1: single-step only
+  rtm::RunConfig defaults;  // launch configuration when no tuned entry matches
+  std::map<rtm::TuneKey, rtm::RunConfig> tuned;  // autotuner results (guarded by mu)
   int *h_err = nullptr;     // pinned: device wait-timeout flag of the last call
   rtm_stats stats{};        // guarded by mu
   rtm_server *server = nullptr;
@@ -77,7 +97,8 @@ int check_opts(rtm_ctx *ctx, const rtm_opts *o);
 // batch size B (items in flight).  Memory is allocated from the pool.
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
-                   int B, cudaStream_t st);
+                   int B, cudaStream_t st, const RunConfig &cfg);
+RunConfig config_for(rtm_ctx *ctx, const rtm_grid &gr, const rtm_opts &op);
 
 // Velocity range check (CFL of §3, positivity, finiteness); synchronises st.
 int check_velocity(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d, long long n,

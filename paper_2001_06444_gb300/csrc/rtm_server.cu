@@ -59,7 +59,7 @@ static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_sta
   if (!rc) rc = check_velocity(ctx, q->r.grid, q->r.vel, (long long)q->r.grid.nx * q->r.grid.nz, st);
   if (!rc)
     rc = migrate_device(ctx, q->r.grid, 1, q->r.vel, q->r.acq, q->r.seis, q->r.opts, q->r.image,
-                        B, st);
+                        B, st, config_for(ctx, q->r.grid, q->r.opts));
   if (st) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) {
@@ -144,7 +144,9 @@ int rtm_server_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket) {
   q->plan = plan_migration(req->grid, req->acq, req->opts, 1);
   q->need1 = q->plan.shared_bytes + q->plan.item_bytes;
   long long nb = a.nshot;
-  if (ctx->max_batch > 0 && nb > ctx->max_batch) nb = ctx->max_batch;
+  const RunConfig cfg = config_for(ctx, req->grid, req->opts);
+  const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
+  if (cap > 0 && nb > cap) nb = cap;
   q->want = q->plan.shared_bytes + (size_t)nb * q->plan.item_bytes;
   if (q->need1 > ctx->budget)
     return fail(ctx, RTM_ERR_NOMEM, "request needs %.3f GB, budget is %.3f GB", q->need1 / 1e9,

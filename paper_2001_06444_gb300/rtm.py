@@ -25,7 +25,7 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 
 # every entry point the header declares
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
-           "rtm_ctx_stats", "rtm_plan_bytes", "rtm_model", "rtm_migrate",
+           "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
            "rtm_poll", "rtm_model_noalloc", "rtm_last_error", "rtm_cfl_limit")
 
@@ -92,6 +92,8 @@ def lib():
             L.rtm_last_error.argtypes = [vp]
             L.rtm_last_error.restype = C.c_char_p
             L.rtm_cfl_limit.restype = C.c_double
+            L.rtm_autotune.argtypes = [vp, C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
+                                       C.POINTER(C.c_int), vp]
             L.rtm_model_noalloc.argtypes = [C.POINTER(Grid), vp, C.POINTER(Acq), ip, vp, vp]
             L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
@@ -218,6 +220,14 @@ class Context:
         st = Stats()
         self._check(lib().rtm_ctx_stats(self.h, C.byref(st), int(bool(reset))))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def autotune(self, grid: Grid, acq: Acq, opts: Opts, trial_steps: int = 64) -> dict:
+        """Time the launch configurations on short synthetic trials and keep
+        the fastest for this shape; returns it."""
+        ch = (C.c_int * 3)()
+        self._check(lib().rtm_autotune(self.h, C.byref(grid), C.byref(acq), C.byref(opts),
+                                       int(trial_steps), ch, C.c_void_p(0)))
+        return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2]}
 
     def model(self, grid: Grid, vel, acq: Acq, shot: int, seis):
         _check_dtype(vel, "float32")
