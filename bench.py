@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--batch", type=int, default=0, help="items in flight (0 = memory budget)")
     p.add_argument("--snap", default="f32", choices=["f32", "bf16", "f16"])
+    p.add_argument("--checkpoint", type=int, default=0,
+                   help="0 keep every snapshot; C>0 / -1 recompute from checkpoints")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the mixed-stream latency run")
@@ -202,7 +204,7 @@ def run_native(args, world, rank, local):
     keep = rtm._Keep()
     acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
     snap = {"f32": rtm.SNAP_F32, "bf16": rtm.SNAP_BF16, "f16": rtm.SNAP_F16}[args.snap]
-    opts = rtm.Opts(4, snap, 1e-6, 1)
+    opts = rtm.Opts(4, snap, 1e-6, 1, args.checkpoint)
 
     vel_true = torch.from_numpy(s.vel.astype(np.float32)).to(dev)
     vel_mig = torch.from_numpy(vm.astype(np.float32)).to(dev)
@@ -301,6 +303,7 @@ def run_native(args, world, rank, local):
             "config": {"workload": WORKLOAD if (s.nshot, s.nt) == (96, 5000)
                        else f"rtm_1701x351_{s.nshot}shots_nt{s.nt}_isnap4_{args.snap}snap", "grid": "1701x351 +20 sponge, 10 m", "shots": s.nshot,
                        "nt": s.nt, "isnap": 4, "snap_dtype": args.snap,
+                       "checkpoint": args.checkpoint,
                        "items_in_flight": args.batch or "memory budget",
                        "launch_config": tuned,
                        "l2": "inputs larger than L2 (3.0 GB snapshot store per shot)",

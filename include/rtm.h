@@ -99,12 +99,18 @@ typedef struct {
 /* Migration options.  isnap: imaging interval (>= 1); snap_dtype: RTM_SNAP_*,
  * storage of the forward snapshots S^k (F16: q = RN(S/s), s = max|S^k| / 2^15;
  * BF16: s = max|S^k|; F32: exact); eps: stabiliser of the source
- * normalisation of Eq. 5 (typical 1e-6); laplacian: 1 applies the §3 filter. */
+ * normalisation of Eq. 5 (typical 1e-6); laplacian: 1 applies the §3 filter.
+ * checkpoint: 0 keeps every snapshot of a shot on the device; C > 0 keeps
+ * only the wavefield state every C steps (C rounded up to even) and, in the
+ * backward pass, recomputes each C-step segment's snapshots from its state
+ * before imaging it, trading one extra forward pass for memory (the image is
+ * bit-identical); -1 picks the C that needs the least memory. */
 typedef struct {
   int isnap;
   int snap_dtype;
   double eps;
   int laplacian;
+  int checkpoint;
 } rtm_opts;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
@@ -253,6 +259,15 @@ int rtm_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms);
  * arguments or host pointers, RTM_ERR_CFL, RTM_ERR_CUDA. */
 int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const rtm_acq *acq,
                       int shot, float *seis, void *stream);
+
+/* Self-test of device-side failure detection (no counterpart in the paper).
+ * The propagation kernels wait on an mbarrier for their TMA copies with a
+ * bound of about one second; a wait that runs out raises an error flag and
+ * the block returns, so the context stays usable.  This call runs the same
+ * bounded wait on a barrier that no copy will complete, for wait_ms
+ * milliseconds, and stores in *raised 1 if the flag came back to the host.
+ * Synchronises the stream. */
+int rtm_selftest_wait(rtm_ctx *ctx, int wait_ms, int *raised, void *stream);
 
 /* Text of the last error on this context (never NULL). */
 const char *rtm_last_error(rtm_ctx *ctx);

@@ -110,14 +110,39 @@ Coef make_coef(const rtm_grid &gr) {
 
 static size_t snap_elem_bytes(int dtype) { return dtype == RTM_SNAP_F32 ? 4 : 2; }
 
+// Segment length of checkpoint mode (0 = keep every snapshot).  Even, so
+// two-step launches never straddle a checkpoint; -1 picks the length that
+// minimises checkpoints (2 planes each) plus the snapshot ring.
+int checkpoint_steps(const rtm_opts &op, const rtm_grid &gr, const Geo &g) {
+  if (op.checkpoint == 0) return 0;
+  long long c = op.checkpoint;
+  if (c < 0) {
+    const double esz = op.snap_dtype == RTM_SNAP_F32 ? 4.0 : 2.0;
+    c = (long long)std::llround(
+        std::sqrt(2.0 * (double)g.plane * gr.nt * op.isnap / ((double)g.pplane * esz)));
+  }
+  c += c & 1;
+  if (c < 2) c = 2;
+  return c >= gr.nt ? 0 : (int)c;
+}
+
 MigrationPlan plan_migration(const rtm_grid &gr, const rtm_acq &acq, const rtm_opts &op,
                              int nsample) {
   MigrationPlan p;
   p.g = make_geo(gr);
   p.nsnap = gr.nt / op.isnap;
   const Geo &g = p.g;
-  p.item_bytes = 4 * (size_t)g.plane * 4 + (size_t)p.nsnap * g.pplane * snap_elem_bytes(op.snap_dtype) +
-                 2 * (size_t)g.pplane * 4 + (size_t)(p.nsnap + 1) * 4 + 256 * 6;
+  const int cpC = checkpoint_steps(op, gr, g);
+  if (!cpC) {
+    p.item_bytes = 4 * (size_t)g.plane * 4 +
+                   (size_t)p.nsnap * g.pplane * snap_elem_bytes(op.snap_dtype) +
+                   2 * (size_t)g.pplane * 4 + (size_t)(p.nsnap + 1) * 4 + 256 * 6;
+  } else {  // two field sets, the checkpoints, the snapshot ring
+    const size_t nseg = (gr.nt + cpC - 1) / cpC, ring = cpC / op.isnap + 1;
+    p.item_bytes = 8 * (size_t)g.plane * 4 + nseg * 2 * (size_t)g.plane * 4 +
+                   ring * g.pplane * snap_elem_bytes(op.snap_dtype) + 2 * (size_t)g.pplane * 4 +
+                   (ring + 1) * 4 + 256 * 10;
+  }
   p.shared_bytes = (size_t)nsample * g.plane * 4 + (size_t)g.P * 4 + (size_t)g.NZ * 4 +
                    (size_t)acq.nshot * 8 + (size_t)(g.ntx * g.ntz + 1) * 4 +
                    (size_t)acq.nrec * 40 + (size_t)(g.ntx2 * g.ntz2 + 1) * 8 + (size_t)gr.nt * 4 +
@@ -170,6 +195,7 @@ int check_opts(rtm_ctx *ctx, const rtm_opts *o) {
     return fail(ctx, RTM_ERR_ARG, "snap_dtype must be 0, 1 or 2 (got %d)", o->snap_dtype);
   if (!(o->eps >= 0) || !std::isfinite(o->eps))
     return fail(ctx, RTM_ERR_ARG, "eps must be finite and >= 0");
+  if (o->checkpoint < -1) return fail(ctx, RTM_ERR_ARG, "checkpoint must be >= -1");
   return RTM_OK;
 }
 
@@ -554,12 +580,19 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   }
   CU(C.items.alloc(ctx, items.size() * 4, st));
   CU(cudaMemcpyAsync(C.items.p, items.data(), items.size() * 4, cudaMemcpyHostToDevice, st));
-  Fields F;
-  if ((rc = alloc_fields(ctx, F, g, B, st, cfg.step_kernel))) return rc;
-  DevBuf snap, smax, num, den, dmax, stack, comp;
   const size_t esz = snap_elem_bytes(op.snap_dtype);
-  CU(snap.alloc(ctx, std::max<size_t>((size_t)B * nsnap * g.pplane * esz, 16), st));
-  CU(smax.alloc(ctx, (size_t)B * std::max(nsnap, 1) * 4, st));
+  // checkpoint mode: the state every cpC steps instead of every snapshot;
+  // each segment's snapshots are recomputed into a ring of `ring` slots
+  const int cpC = checkpoint_steps(op, gr, g);
+  const int nseg = cpC ? (gr.nt + cpC - 1) / cpC : 0;
+  const int ring = cpC ? cpC / op.isnap + 1 : nsnap;
+  Fields F, U;  // F: forward fields, then the receiver wavefield; U: recomputed forward
+  if ((rc = alloc_fields(ctx, F, g, B, st, cfg.step_kernel))) return rc;
+  if (cpC && (rc = alloc_fields(ctx, U, g, B, st, cfg.step_kernel))) return rc;
+  DevBuf snap, smax, num, den, dmax, stack, comp, cps;
+  CU(snap.alloc(ctx, std::max<size_t>((size_t)B * ring * g.pplane * esz, 16), st));
+  CU(smax.alloc(ctx, (size_t)B * std::max(ring, 1) * 4, st));
+  if (cpC) CU(cps.alloc(ctx, (size_t)nseg * 2 * B * g.plane * 4, st));
   CU(num.alloc(ctx, (size_t)B * g.pplane * 4, st));
   CU(den.alloc(ctx, (size_t)B * g.pplane * 4, st));
   CU(dmax.alloc(ctx, (size_t)B * 4, st));
@@ -571,7 +604,8 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   CU(cudaMemsetAsync(comp.p, 0, comp.bytes, st));
 
   // algorithmic bytes per item (16 B per padded update; b per physical pixel
-  // per snapshot written or read; 16 B per physical pixel per imaging step)
+  // per snapshot written or read; 16 B per physical pixel per imaging step);
+  // recomputation in checkpoint mode is overhead, not counted
   const double upd = (double)g.NZ * g.NX, pix = (double)g.nz * g.nx;
   const double fwd_bytes = gr.nt * 16.0 * upd + nsnap * (double)esz * pix;
   const double bwd_bytes = gr.nt * 16.0 * upd + nsnap * ((double)esz + 16.0) * pix;
@@ -591,7 +625,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   A.seis = seis_d;
   A.snap = snap.p;
   A.snap_dtype = op.snap_dtype;
-  A.nsnap = nsnap;
+  A.nsnap = ring;
   A.smax = smax.as<unsigned>();
   A.num = num.as<float>();
   A.den = den.as<float>();
@@ -601,90 +635,130 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   const bool two = cfg.step_kernel == 2;
   const bool graph = cfg.graph != 0;
   auto inK = [&](int m) { return m >= 1 && m <= nt && m % isnap == 0; };
+  int nb = 0;
+  Step2Args A2;
+
+  // Forward steps n0 .. n1-1 on Fs.  store: keep S^k, k in K and n0 < k <= n1,
+  // in slot k/isnap - 1 - kbase.  save: copy the state into checkpoint n/cpC
+  // before every step n that is a multiple of cpC.
+  auto fwd_range = [&](Fields &Fs, int n0, int n1, int kbase, bool store, bool save) -> int {
+    int r2;
+    auto idx = [&](int k) { return k / isnap - 1 - kbase; };
+    bool stored = true;  // the range's input field is not the range's to store
+    for (int n = n0; n < n1;) {
+      if (save && n % cpC == 0) {
+        const size_t bytes = (size_t)nb * g.plane * 4;
+        float *dst = cps.as<float>() + (size_t)(n / cpC) * 2 * B * g.plane;
+        CU(cudaMemcpyAsync(dst, Fs.v[Fs.cv].p, bytes, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(dst + (size_t)B * g.plane, Fs.d[Fs.cd].p, bytes,
+                           cudaMemcpyDeviceToDevice, st));
+      }
+      if (two && n + 2 <= n1 && (!half || isnap % 2 == 0)) {
+        Step2RT r;
+        r.t1 = n;
+        r.t2 = n + 1;
+        r.snap_in_idx = (store && inK(n) && !stored) ? idx(n) : -1;
+        r.snap_mid_idx = (store && !half && inK(n + 1)) ? idx(n + 1) : -1;
+        r.snap_out_idx = (store && !half && inK(n + 2)) ? idx(n + 2) : -1;
+        r.max_out_idx = (store && half && inK(n + 2)) ? idx(n + 2) : -1;
+        r.img_mid_idx = r.img_out_idx = -1;
+        r.dmax_flag = 0;
+        if ((r2 = step2(ctx, MODE_FWD, A2, C, Fs, r, nb, st))) return r2;
+        stored = !half;
+        n += 2;
+      } else {
+        StepRT r{};
+        r.n = n;
+        r.snap_idx = (store && inK(n) && !stored) ? idx(n) : -1;
+        r.max_idx = (store && half && inK(n + 1)) ? idx(n + 1) : -1;
+        r.img_idx = -1;
+        r.dmax_flag = 0;
+        if ((r2 = step1(ctx, MODE_FWD, A, Fs, r, nb, st))) return r2;
+        stored = false;
+        n += 1;
+      }
+      ++step_launches;
+    }
+    if (store && inK(n1) && !stored) {
+      CU(launch_snap_store(A, Fs.v[Fs.cv].as<float>(), idx(n1), nb, st));
+      ++launches;
+    }
+    return RTM_OK;
+  };
+  // Backward steps k = k1 .. k0+1 on Ws, imaging with slot k/isnap - 1 - kbase.
+  auto bwd_range = [&](Fields &Ws, int k1, int k0, int kbase) -> int {
+    int r2;
+    auto idx = [&](int k) { return k / isnap - 1 - kbase; };
+    for (int k = k1; k > k0;) {
+      if (two && k - 1 > k0) {
+        Step2RT r;
+        r.t1 = k - 1;
+        r.t2 = k - 2;
+        r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+        r.img_mid_idx = inK(k) ? idx(k) : -1;
+        r.img_out_idx = inK(k - 1) ? idx(k - 1) : -1;
+        r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
+        if ((r2 = step2(ctx, MODE_BWD, A2, C, Ws, r, nb, st))) return r2;
+        k -= 2;
+      } else {
+        StepRT r{};
+        r.n = k;
+        r.snap_idx = r.max_idx = -1;
+        r.img_idx = inK(k) ? idx(k) : -1;
+        r.dmax_flag = (k == isnap) ? 1 : 0;
+        if ((r2 = step1(ctx, MODE_BWD, A, Ws, r, nb, st))) return r2;
+        k -= 1;
+      }
+      ++step_launches;
+    }
+    return RTM_OK;
+  };
+
   for (long long q0 = 0; q0 < nitems; q0 += B) {
-    const int nb = (int)std::min<long long>(B, nitems - q0);
+    nb = (int)std::min<long long>(B, nitems - q0);
     A.item_sample = C.items.as<int>() + q0;
     A.item_shot = C.items.as<int>() + nitems + q0;
-    Step2Args A2;
     fill_args2(A2, A, C);
     if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
     CU(cudaMemsetAsync(smax.p, 0, smax.bytes, st));
     CU(cudaMemsetAsync(dmax.p, 0, dmax.bytes, st));
-    // forward: snapshots S^k, k in K
-    if ((rc = mark())) return rc;
-    bool stored = false;  // the current field, if in K, is already stored
-    long long nlaunch = 0;
-    rc = run_phase(ctx, graph, st, [&]() -> int {
-      int r2;
-      for (int n = 0; n < nt;) {
-        if (two && n + 2 <= nt && (!half || isnap % 2 == 0)) {
-          Step2RT r;
-          r.t1 = n;
-          r.t2 = n + 1;
-          r.snap_in_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
-          r.snap_mid_idx = (!half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
-          r.snap_out_idx = (!half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
-          r.max_out_idx = (half && inK(n + 2)) ? (n + 2) / isnap - 1 : -1;
-          r.img_mid_idx = r.img_out_idx = -1;
-          r.dmax_flag = 0;
-          if ((r2 = step2(ctx, MODE_FWD, A2, C, F, r, nb, st))) return r2;
-          stored = !half;
-          n += 2;
-        } else {
-          StepRT r{};
-          r.n = n;
-          r.snap_idx = (inK(n) && !stored) ? n / isnap - 1 : -1;
-          r.max_idx = (half && inK(n + 1)) ? (n + 1) / isnap - 1 : -1;
-          r.img_idx = -1;
-          r.dmax_flag = 0;
-          if ((r2 = step1(ctx, MODE_FWD, A, F, r, nb, st))) return r2;
-          stored = false;
-          n += 1;
-        }
-        ++nlaunch;
+    if (!cpC) {
+      // forward with every snapshot S^k, k in K; then backward with imaging
+      if ((rc = mark())) return rc;
+      rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, true, false); });
+      if (rc) return rc;
+      if ((rc = mark())) return rc;
+      if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
+      if ((rc = mark())) return rc;
+      rc = run_phase(ctx, graph, st, [&]() { return bwd_range(F, nt, 0, 0); });
+      if (rc) return rc;
+      if ((rc = mark())) return rc;
+    } else {
+      // forward keeping the state every cpC steps; then, segment by segment
+      // from the last, recompute the segment's snapshots from its checkpoint
+      // and run its backward steps (F carries the receiver wavefield across)
+      if ((rc = mark())) return rc;
+      rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, false, true); });
+      if (rc) return rc;
+      if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
+      for (int sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
+        const int n0 = sgi * cpC, n1 = std::min(nt, n0 + cpC), kbase = n0 / isnap;
+        rc = run_phase(ctx, graph, st, [&]() -> int {
+          const size_t bytes = (size_t)nb * g.plane * 4;
+          const float *src = cps.as<float>() + (size_t)sgi * 2 * B * g.plane;
+          CU(cudaMemcpyAsync(U.v[0].p, src, bytes, cudaMemcpyDeviceToDevice, st));
+          CU(cudaMemcpyAsync(U.d[0].p, src + (size_t)B * g.plane, bytes, cudaMemcpyDeviceToDevice,
+                             st));
+          U.cv = U.cd = 0;
+          if (half) CU(cudaMemsetAsync(smax.p, 0, smax.bytes, st));
+          int r2 = fwd_range(U, n0, n1, kbase, true, false);
+          if (!r2) r2 = bwd_range(F, n1, n0, kbase);
+          return r2;
+        });
       }
-      return RTM_OK;
-    });
-    if (rc) return rc;
-    step_launches += nlaunch;
-    if ((rc = mark())) return rc;
-    if (inK(nt) && !stored) {
-      CU(launch_snap_store(A, F.v[F.cv].as<float>(), nt / isnap - 1, nb, st));
-      ++launches;
+      if (rc) return rc;
+      if ((rc = mark())) return rc;
     }
-    // backward: receiver wavefield and imaging
-    if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
-    if ((rc = mark())) return rc;
-    nlaunch = 0;
-    rc = run_phase(ctx, graph, st, [&]() -> int {
-      int r2;
-      for (int k = nt; k >= 1;) {
-        if (two && k >= 2) {
-          Step2RT r;
-          r.t1 = k - 1;
-          r.t2 = k - 2;
-          r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
-          r.img_mid_idx = inK(k) ? k / isnap - 1 : -1;
-          r.img_out_idx = inK(k - 1) ? (k - 1) / isnap - 1 : -1;
-          r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
-          if ((r2 = step2(ctx, MODE_BWD, A2, C, F, r, nb, st))) return r2;
-          k -= 2;
-        } else {
-          StepRT r{};
-          r.n = k;
-          r.snap_idx = r.max_idx = -1;
-          r.img_idx = inK(k) ? k / isnap - 1 : -1;
-          r.dmax_flag = (k == isnap) ? 1 : 0;
-          if ((r2 = step1(ctx, MODE_BWD, A, F, r, nb, st))) return r2;
-          k -= 1;
-        }
-        ++nlaunch;
-      }
-      return RTM_OK;
-    });
-    if (rc) return rc;
-    step_launches += nlaunch;
-    if ((rc = mark())) return rc;
     CU(launch_norm_stack(A.num, A.den, A.dmax, A.item_sample, nb, (float)op.eps, g.pplane,
                          stack.as<float>(), comp.as<float>(), st));
     launches += 1;
@@ -1021,6 +1095,22 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
     choice[1] = cand[best].max_items;
     choice[2] = cand[best].graph;
   }
+  return RTM_OK;
+}
+
+int rtm_selftest_wait(rtm_ctx *ctx, int wait_ms, int *raised, void *stream) {
+  if (!ctx || !raised || wait_ms < 1 || wait_ms > 10000) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = set_device(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf f;
+  CU(f.alloc(ctx, 16, st));
+  CU(cudaMemsetAsync(f.p, 0, 16, st));
+  CU(launch_wait_probe(f.as<int>(), (unsigned long long)wait_ms * 1000000ull, st));
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, f.p, 4, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *raised = h;
   return RTM_OK;
 }
 

@@ -78,6 +78,7 @@ struct DevBuf {
 bool is_device_ptr(const void *p);
 
 Geo make_geo(const rtm_grid &gr);
+int checkpoint_steps(const rtm_opts &op, const rtm_grid &gr, const Geo &g);
 Coef make_coef(const rtm_grid &gr);
 
 struct MigrationPlan {

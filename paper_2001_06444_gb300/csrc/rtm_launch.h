@@ -21,6 +21,8 @@ cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                          cudaStream_t st);
 size_t step2_smem_bytes();
+// bounded-wait self-test: raises *flag after waiting `ns` for bytes that never arrive
+cudaError_t launch_wait_probe(int *flag, unsigned long long ns, cudaStream_t st);
 int step2_tile_x();
 int step2_tile_z();
 int step2_ext();

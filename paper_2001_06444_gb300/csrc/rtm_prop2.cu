@@ -41,7 +41,7 @@ constexpr int EX = C2X + 8, EZ = C2Z + 8;     // extended region (halo 4)
 constexpr int VX = C2X + 16, VZ = C2Z + 16;   // v^n tile (halo 8)
 constexpr int NTH = 256;                      // 32 x 8 threads
 constexpr unsigned kTxBytes = (VX * VZ + 2 * EX * EZ) * 4;
-constexpr unsigned kWaitLimit = 1u << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of a device-side wait: 1 s
 
 struct Smem {
   float v0[VZ][VX];   // v^n            (TMA destination)
@@ -80,6 +80,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
       : "r"(smem_u32(bar)), "r"(phase)
       : "memory");
   return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the mbarrier phase to complete, for at most `ns` nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase,
+                                                  unsigned long long ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, phase))
+    if (global_ns() - t0 > ns) return false;
+  return true;
 }
 
 // Quantised store / load of 4 consecutive physical values (same encoding as
@@ -269,22 +285,11 @@ __global__ void __launch_bounds__(NTH, 3)
       }
     }
   }
-  {
-    unsigned it = 0;
-    bool ok = true;
-    while (!mbar_try_wait(&S.bar, 0)) {
-      if (++it > kWaitLimit) {
-        ok = false;
-        break;
-      }
-    }
-    if (!ok) {
-      if (tid == 0) atomicExch(A.err, 1);
-      // let the copies in flight land (bounded) before the block exits
-      for (unsigned j = 0; j < kWaitLimit && !mbar_try_wait(&S.bar, 0); ++j) {
-      }
-      return;
-    }
+  if (!mbar_wait_bounded(&S.bar, 0, kWaitNs)) {
+    if (tid == 0) atomicExch(A.err, 1);
+    // let the copies in flight land (bounded) before the block exits
+    mbar_wait_bounded(&S.bar, 0, kWaitNs);
+    return;
   }
 
   const bool interior = (z0 - 4 >= g.nb) && (z0 + C2Z + 4 <= g.NZ - g.nb) &&
@@ -566,6 +571,29 @@ __global__ void __launch_bounds__(NTH, 3)
   if (MODE == MODE_FWD && rt.max_out_idx >= 0)
     block_max_atomic(mx, &A.smax[(long long)b * A.nsnap + rt.max_out_idx], S.red);
   if (MODE == MODE_BWD && rt.dmax_flag == 2) block_max_atomic(dm, &A.dmax[b], S.red);
+}
+
+// Self-test of the bounded wait: one block arms an mbarrier for bytes that no
+// copy will deliver (nothing is issued), so its wait runs out after the bound
+// and it raises the flag, exactly as k_step2 does when a TMA transaction never
+// completes.  Touches nothing but its own shared memory and the flag.
+__global__ void k_wait_probe(int *flag, unsigned long long ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
+                 "r"(16u)
+                 : "memory");
+  if (!mbar_wait_bounded(&bar, 0, ns) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+cudaError_t launch_wait_probe(int *flag, unsigned long long ns, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(flag, ns);
+  return cudaGetLastError();
 }
 
 size_t step2_smem_bytes() { return sizeof(Smem) + 128; }

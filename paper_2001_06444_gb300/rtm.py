@@ -27,7 +27,8 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
-           "rtm_poll", "rtm_model_noalloc", "rtm_last_error", "rtm_cfl_limit")
+           "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_last_error",
+           "rtm_cfl_limit")
 
 
 class RTMError(RuntimeError):
@@ -48,8 +49,11 @@ class Acq(C.Structure):
 
 
 class Opts(C.Structure):
+    """isnap, snap_dtype, eps, laplacian, checkpoint (0 = keep every snapshot,
+    C > 0 = keep the state every C steps and recompute, -1 = least memory)."""
+
     _fields_ = [("isnap", C.c_int), ("snap_dtype", C.c_int), ("eps", C.c_double),
-                ("laplacian", C.c_int)]
+                ("laplacian", C.c_int), ("checkpoint", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -94,6 +98,7 @@ def lib():
             L.rtm_cfl_limit.restype = C.c_double
             L.rtm_autotune.argtypes = [vp, C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                        C.POINTER(C.c_int), vp]
+            L.rtm_selftest_wait.argtypes = [vp, ip, C.POINTER(ip), vp]
             L.rtm_model_noalloc.argtypes = [C.POINTER(Grid), vp, C.POINTER(Acq), ip, vp, vp]
             L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
@@ -228,6 +233,13 @@ class Context:
         self._check(lib().rtm_autotune(self.h, C.byref(grid), C.byref(acq), C.byref(opts),
                                        int(trial_steps), ch, C.c_void_p(0)))
         return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2]}
+
+    def selftest_wait(self, wait_ms: int = 200) -> bool:
+        """Run the bounded device-side wait on a barrier nothing completes;
+        True if its error flag reached the host."""
+        r = C.c_int(0)
+        self._check(lib().rtm_selftest_wait(self.h, int(wait_ms), C.byref(r), C.c_void_p(0)))
+        return bool(r.value)
 
     def model(self, grid: Grid, vel, acq: Acq, shot: int, seis):
         _check_dtype(vel, "float32")
