@@ -23,7 +23,7 @@ import numpy as np
 from .stats import ensemble_stats, uncertainty_maps  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "rtm_oracle.c")
+_SRCS = [os.path.join(_HERE, "rtm_oracle.c"), os.path.join(_HERE, "codec_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -43,11 +43,11 @@ def build(force: bool = False) -> str:
     """Compile the C oracle into ``oracle/_build/liboracle.so``."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", "-ffp-contract=off", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -78,6 +78,16 @@ def lib():
             L.oracle_courant.restype = C.c_double
             L.oracle_sponge.argtypes = [g, dp]
             L.oracle_threads.restype = C.c_int
+            L.oracle_codec_kmin.argtypes = [C.c_double, C.c_int]
+            L.oracle_codec_transform.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.oracle_codec_transform.restype = None
+            L.oracle_codec_bound.argtypes = [C.c_int64, C.c_int64]
+            L.oracle_codec_bound.restype = C.c_uint64
+            L.oracle_codec_compress.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double,
+                                                C.c_void_p, C.c_uint64]
+            L.oracle_codec_compress.restype = C.c_uint64
+            L.oracle_codec_decompress.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
+                                                  C.c_int64]
             _lib = L
     return _lib
 
@@ -208,3 +218,40 @@ def sponge(g: Grid):
 def threads() -> int:
     """Threads the oracle's OpenMP loops use."""
     return int(lib().oracle_threads())
+
+
+# ---------------------------------------------------------------- codec --
+
+def codec_kmin(tol, e) -> int:
+    """Lowest bit plane the codec keeps for tolerance tol, block exponent e."""
+    return int(lib().oracle_codec_kmin(float(tol), int(e)))
+
+
+def codec_transform(block):
+    """(forward, forward-then-inverse) integer transform of a 4 x 4 int32 block."""
+    q = np.ascontiguousarray(np.asarray(block, np.int32).reshape(16))
+    f = np.zeros(16, np.int32)
+    b = np.zeros(16, np.int32)
+    lib().oracle_codec_transform(q.ctypes.data, f.ctypes.data, b.ctypes.data)
+    return f.reshape(4, 4), b.reshape(4, 4)
+
+
+def codec_compress(data, tol) -> bytes:
+    """Compressed stream of a 2D float32 array with absolute tolerance tol."""
+    a = np.ascontiguousarray(np.asarray(data, np.float32))
+    n0, n1 = a.shape
+    cap = int(lib().oracle_codec_bound(n0, n1))
+    out = np.zeros(cap, np.uint8)
+    n = int(lib().oracle_codec_compress(a.ctypes.data, n0, n1, float(tol), out.ctypes.data, cap))
+    if n == 0:
+        raise ValueError("bad codec arguments")
+    return out[:n].tobytes()
+
+
+def codec_decompress(blob: bytes, n0, n1):
+    buf = np.frombuffer(blob, np.uint8).copy()
+    out = np.zeros((n0, n1), np.float32)
+    rc = lib().oracle_codec_decompress(buf.ctypes.data, buf.size, out.ctypes.data, int(n0), int(n1))
+    if rc:
+        raise ValueError(f"corrupt stream ({rc})")
+    return out
