@@ -228,23 +228,29 @@ def codec_kmin(tol, e) -> int:
 
 
 def codec_transform(block):
-    """(forward, forward-then-inverse) integer transform of a 4 x 4 int32 block."""
-    q = np.ascontiguousarray(np.asarray(block, np.int32).reshape(16))
-    f = np.zeros(16, np.int32)
-    b = np.zeros(16, np.int32)
+    """(forward, forward-then-inverse) integer transform of a 4 x 4 integer block."""
+    q = np.ascontiguousarray(np.asarray(block, np.int64).reshape(16))
+    f = np.zeros(16, np.int64)
+    b = np.zeros(16, np.int64)
     lib().oracle_codec_transform(q.ctypes.data, f.ctypes.data, b.ctypes.data)
     return f.reshape(4, 4), b.reshape(4, 4)
 
 
+def codec_bound(n0, n1) -> int:
+    """Upper bound of the stream size in bytes of an n0 x n1 array."""
+    return int(lib().oracle_codec_bound(int(n0), int(n1)))
+
+
 def codec_compress(data, tol) -> bytes:
-    """Compressed stream of a 2D float32 array with absolute tolerance tol."""
+    """Compressed stream of a 2D float32 array: absolute tolerance tol > 0,
+    or lossless with tol == 0."""
     a = np.ascontiguousarray(np.asarray(data, np.float32))
     n0, n1 = a.shape
     cap = int(lib().oracle_codec_bound(n0, n1))
     out = np.zeros(cap, np.uint8)
     n = int(lib().oracle_codec_compress(a.ctypes.data, n0, n1, float(tol), out.ctypes.data, cap))
     if n == 0:
-        raise ValueError("bad codec arguments")
+        raise ValueError("bad codec arguments (or a non-finite value with tol > 0)")
     return out[:n].tobytes()
 
 
