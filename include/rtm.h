@@ -136,7 +136,10 @@ int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items);
  * point update (read u^n, u^{n-1}, c; write u^{n+1}), plus b per physical
  * pixel for each snapshot stored or read (b = 4 or 2) and 16 B per physical
  * pixel per imaging step (num and den read and written).  launches counts
- * every kernel the library launched. */
+ * every kernel the library launched.  codec_ms and codec_bytes are the same
+ * for the codec kernels of rtm_compress / rtm_decompress: device time of
+ * each kernel, and its algorithmic bytes (the floats read or written plus
+ * the stream bytes written or read). */
 typedef struct {
   long long step_launches;
   double step_ms;
@@ -144,6 +147,9 @@ typedef struct {
   double point_updates;
   long long launches;
   long long migrations;
+  long long codec_launches;
+  double codec_ms;
+  double codec_bytes;
 } rtm_stats;
 
 /* Turn profiling on (1) or off (0).  With profiling on, every migration
@@ -268,6 +274,46 @@ int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const rtm_acq *acq
  * milliseconds, and stores in *raised 1 if the flag came back to the host.
  * Synchronises the stream. */
 int rtm_selftest_wait(rtm_ctx *ctx, int wait_ms, int *raised, void *stream);
+
+/* ------------------------------------------------------------- codec --
+ * Error-bounded compression of velocity models, images and seismograms
+ * (§3 and §4.2, Tables 1-2: the workflow stores and moves its arrays
+ * through a transform block codec, in a fixed-accuracy mode with an absolute
+ * tolerance and in a lossless mode).  Each n0 x n1 float array (row-major)
+ * becomes one stream: 4 x 4 blocks, a block exponent and 28-bit fixed point
+ * (fixed accuracy) or the float bits as order-preserving integers
+ * (lossless), an exactly reversible integer transform, and bit-plane coding
+ * of the coefficients down to the lowest plane the tolerance needs.  Fixed
+ * accuracy returns every element within max(tol, 2^(e-23)) of its input,
+ * where max |x| over its block is f 2^e with f in [0.5, 1); lossless returns
+ * the input bits exactly (NaN, infinities and -0 included).  The stream
+ * layout (header, chunk index, bit section) is given in the library's codec
+ * source.  Both calls synchronise the stream before they return. */
+
+/* Bytes one stream of an n0 x n1 array can take at most (0 if the shape is
+ * not supported: n0, n1 >= 1 and fewer than 2^32 / 20 blocks of 4 x 4). */
+uint64_t rtm_compress_bound(long long n0, long long n1);
+
+/* Compress count arrays data [count][n0][n1] (host or device).  tol > 0:
+ * fixed accuracy with absolute tolerance tol; tol == 0: lossless.  Stream i
+ * is written at out + i * out_stride (host or device; out_stride >=
+ * rtm_compress_bound(n0, n1), a multiple of 16; out 16-byte aligned) and its
+ * byte count to out_bytes[i] (host).  An array holding a NaN or an infinity
+ * cannot be coded with tol > 0: its out_bytes is 0 and the call returns
+ * RTM_ERR_ARG after coding the others.  RTM_ERR_TIMEOUT if a device-side
+ * wait gave up (nothing usable is written then). */
+int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0, long long n1,
+                 double tol, void *out, uint64_t out_stride, uint64_t *out_bytes,
+                 void *stream);
+
+/* Decompress count streams in + i * in_stride (host or device; in_stride a
+ * multiple of 16 and at least the stream's bytes; in 16-byte aligned) into
+ * data [count][n0][n1] (host or device); count <= 65535.  The mode and the
+ * tolerance come from each stream's header.  RTM_ERR_ARG names the first
+ * stream that is malformed or was not made for n0 x n1 (the elements of its
+ * damaged chunks are then unspecified). */
+int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long count,
+                   long long n0, long long n1, float *data, void *stream);
 
 /* Text of the last error on this context (never NULL). */
 const char *rtm_last_error(rtm_ctx *ctx);

@@ -27,8 +27,8 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
-           "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_last_error",
-           "rtm_cfl_limit")
+           "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
+           "rtm_compress", "rtm_decompress", "rtm_last_error", "rtm_cfl_limit")
 
 
 class RTMError(RuntimeError):
@@ -59,7 +59,9 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("step_launches", C.c_longlong), ("step_ms", C.c_double),
                 ("step_bytes", C.c_double), ("point_updates", C.c_double),
-                ("launches", C.c_longlong), ("migrations", C.c_longlong)]
+                ("launches", C.c_longlong), ("migrations", C.c_longlong),
+                ("codec_launches", C.c_longlong), ("codec_ms", C.c_double),
+                ("codec_bytes", C.c_double)]
 
 
 class Request(C.Structure):
@@ -100,6 +102,12 @@ def lib():
                                        C.POINTER(C.c_int), vp]
             L.rtm_selftest_wait.argtypes = [vp, ip, C.POINTER(ip), vp]
             L.rtm_model_noalloc.argtypes = [C.POINTER(Grid), vp, C.POINTER(Acq), ip, vp, vp]
+            ll, u64 = C.c_longlong, C.c_uint64
+            L.rtm_compress_bound.argtypes = [ll, ll]
+            L.rtm_compress_bound.restype = u64
+            L.rtm_compress.argtypes = [vp, vp, ll, ll, ll, C.c_double, vp, u64,
+                                       C.POINTER(u64), vp]
+            L.rtm_decompress.argtypes = [vp, vp, u64, ll, ll, ll, vp, vp]
             L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
             _lib = L
@@ -178,6 +186,14 @@ def _stream(*arrays):
 
             return C.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
     return C.c_void_p(0)
+
+
+def compress_bound(n0: int, n1: int) -> int:
+    """Bytes one compressed n0 x n1 stream can take at most."""
+    b = int(lib().rtm_compress_bound(int(n0), int(n1)))
+    if not b:
+        raise ValueError(f"unsupported shape {n0} x {n1}")
+    return b
 
 
 class Context:
@@ -281,6 +297,39 @@ class Context:
         self._check(lib().rtm_ensemble_stats(self.h, ptrs[0], n, npix, *ptrs[1:],
                                              _stream(images, mean, std, q05, q95)))
         return mean, std, q05, q95
+
+    def compress(self, data, tol: float, out=None, stride: int = 0):
+        """Compress data [count][n0][n1] (or [n0][n1]) float32, host or
+        device: absolute tolerance tol > 0, lossless with tol == 0.  Streams
+        go to out (uint8, host or device, count * stride bytes; allocated on
+        data's device when None) at a stride of compress_bound(n0, n1)
+        rounded up to 16 unless given.  Returns (out, stride, byte counts)."""
+        _check_dtype(data, "float32")
+        shape = tuple(int(v) for v in data.shape)
+        count, n0, n1 = (1, *shape) if len(shape) == 2 else shape
+        if not stride:
+            stride = (compress_bound(n0, n1) + 15) // 16 * 16
+        if out is None:
+            if getattr(data, "is_cuda", False):
+                import torch
+
+                out = torch.empty(count * stride, dtype=torch.uint8, device=data.device)
+            else:
+                out = np.empty(count * stride, np.uint8)
+        sizes = (C.c_uint64 * count)()
+        self._check(lib().rtm_compress(self.h, C.c_void_p(_ptr(data)[0]), count, n0, n1,
+                                       float(tol), C.c_void_p(_ptr(out)[0]), int(stride), sizes,
+                                       _stream(data, out)))
+        return out, stride, [int(v) for v in sizes]
+
+    def decompress(self, streams, stride: int, count: int, n0: int, n1: int, out):
+        """Decompress count streams (uint8, host or device, at the given
+        stride) into out [count][n0][n1] float32 (host or device)."""
+        _check_dtype(out, "float32")
+        self._check(lib().rtm_decompress(self.h, C.c_void_p(_ptr(streams)[0]), int(stride),
+                                         int(count), int(n0), int(n1),
+                                         C.c_void_p(_ptr(out)[0]), _stream(streams, out)))
+        return out
 
     def uncertainty_maps(self, mean, std, conf, ratio):
         npix = int(np.prod(mean.shape))

@@ -1,0 +1,137 @@
+"""GPU codec (rtm_compress / rtm_decompress) against the codec oracle:
+streams byte-identical, decoded arrays bit-identical, on ragged shapes that
+span several chunks and tiles, in both modes, through device and host
+pointers; at full size (one 5000 x 1701 seismogram at the paper's 1e-4
+tolerance, and a batch of images) byte-identical streams too; malformed
+streams and non-finite inputs are reported."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_06444_gb300 import inputs, rtm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rtm.Context(0)
+    yield c
+    c.close()
+
+
+def _arrays(seed, count, n0, n1, kind):
+    if kind == "normal":
+        a = inputs.normal(seed, count * n0 * n1).reshape(count, n0, n1) * 3.0
+        a[:, 1, :] *= 1e-5
+        return a.astype(np.float32)
+    if kind == "smooth":
+        out = np.stack([inputs.smooth(inputs.layered_faulted(n0, n1, 10.0, 10.0, seed=seed + i),
+                                      10, 10, 30.0) for i in range(count)])
+        return out.astype(np.float32)
+    bits = (inputs.uniform(seed, count * n0 * n1) * 2 ** 32).astype(np.uint64).astype(np.uint32)
+    return bits.view(np.float32).reshape(count, n0, n1).copy()
+
+
+def _check_against_oracle(ctx, x, tol, via_host=False):
+    count, n0, n1 = x.shape
+    data = x if via_host else torch.from_numpy(x).cuda()
+    out, stride, sizes = ctx.compress(data, tol)
+    blob = out if via_host else out.cpu().numpy()
+    dec = np.zeros_like(x) if via_host else torch.zeros(x.shape, dtype=torch.float32,
+                                                         device="cuda")
+    ctx.decompress(out, stride, count, n0, n1, dec)
+    dec = dec if via_host else dec.cpu().numpy()
+    for i in range(count):
+        want = oracle.codec_compress(x[i], tol)
+        got = blob[i * stride:i * stride + sizes[i]].tobytes()
+        assert sizes[i] == len(want), (i, sizes[i], len(want))
+        assert got == want, i
+        ref = oracle.codec_decompress(want, n0, n1)
+        assert np.array_equal(dec[i].view(np.uint32), ref.view(np.uint32)), i
+    return sizes
+
+
+@pytest.mark.parametrize("shape", [(1, 4, 4), (3, 23, 38), (2, 130, 301), (1, 257, 1030)])
+@pytest.mark.parametrize("kind,tols", [("normal", (1e-6, 1e-3, 0.5, 0.0)),
+                                       ("smooth", (1e-4, 1e-1, 0.0)),
+                                       ("bits", (0.0,))])
+def test_streams_identical_to_oracle(ctx, shape, kind, tols):
+    x = _arrays(7, *shape, kind)
+    for tol in tols:
+        _check_against_oracle(ctx, x, tol)
+
+
+def test_host_pointers(ctx):
+    x = _arrays(9, 2, 61, 77, "normal")
+    _check_against_oracle(ctx, x, 1e-3, via_host=True)
+    _check_against_oracle(ctx, x, 0.0, via_host=True)
+
+
+def test_full_size_seismogram_and_images(ctx):
+    # one shot of the 1701-receiver, 5000-sample survey (§4.2 compresses
+    # seismograms at 1e-4) and 8 images of the 1701 x 351 grid
+    nt, nrec = 5000, 1701
+    seis = inputs.normal(21, nt * nrec).reshape(1, nt, nrec).astype(np.float32)
+    t = np.arange(nt)[:, None]
+    seis[0] *= np.exp(-t / 1500.0).astype(np.float32) * 1e-3  # decaying traces
+    sizes = _check_against_oracle(ctx, seis, 1e-4)
+    assert sizes[0] < seis.nbytes
+    imgs = _arrays(31, 8, 351, 1701, "smooth")
+    _check_against_oracle(ctx, imgs, 1e-1)
+
+
+def test_error_bound_and_lossless_on_device(ctx):
+    x = _arrays(41, 4, 300, 517, "normal")
+    for tol in (1e-2, 1e-5):
+        d = torch.from_numpy(x).cuda()
+        out, stride, sizes = ctx.compress(d, tol)
+        y = torch.zeros_like(d)
+        ctx.decompress(out, stride, 4, 300, 517, y)
+        err = (y - d).abs().cpu().numpy()
+        mx = np.abs(x).max()
+        assert err.max() <= max(tol, 2.0 ** (np.frexp(mx)[1] - 23))
+    bits = _arrays(43, 2, 100, 90, "bits")
+    d = torch.from_numpy(bits).cuda()
+    out, stride, sizes = ctx.compress(d, 0.0)
+    y = torch.zeros_like(d)
+    ctx.decompress(out, stride, 2, 100, 90, y)
+    assert torch.equal(y.view(torch.int32), d.view(torch.int32))
+
+
+def test_nonfinite_and_malformed_are_reported(ctx):
+    x = _arrays(51, 3, 40, 40, "normal")
+    x[1, 7, 9] = np.inf
+    d = torch.from_numpy(x).cuda()
+    with pytest.raises(rtm.RTMError) as ei:
+        ctx.compress(d, 1e-3)
+    assert ei.value.code == rtm.RTM_ERR_ARG
+    stride = (rtm.compress_bound(40, 40) + 15) // 16 * 16
+    out = torch.zeros(3 * stride, dtype=torch.uint8, device="cuda")
+    sizes = (C.c_uint64 * 3)()
+    rc = rtm.lib().rtm_compress(ctx.h, C.c_void_p(d.data_ptr()), 3, 40, 40, 1e-3,
+                                C.c_void_p(out.data_ptr()), stride, sizes, None)
+    assert rc == rtm.RTM_ERR_ARG and sizes[1] == 0 and sizes[0] > 0 and sizes[2] > 0
+    # the two good streams still decode like the oracle's
+    for i in (0, 2):
+        got = out[i * stride:i * stride + sizes[i]].cpu().numpy().tobytes()
+        assert got == oracle.codec_compress(x[i], 1e-3)
+    # damaged streams: wrong shape, bad magic, a cut bit section
+    good, stride, sizes = ctx.compress(torch.from_numpy(x[[0, 2]]).cuda(), 1e-3)
+    y = torch.zeros((2, 40, 40), dtype=torch.float32, device="cuda")
+    with pytest.raises(rtm.RTMError):
+        ctx.decompress(good, stride, 2, 40, 41, torch.zeros((2, 40, 41), device="cuda"))
+    bad = good.clone()
+    bad[stride] ^= 1
+    with pytest.raises(rtm.RTMError, match="stream 1"):
+        ctx.decompress(bad, stride, 2, 40, 40, y)
+    bad = good.clone()
+    bad[40:48] = torch.tensor(np.frombuffer(np.uint64(3).tobytes(), np.uint8).copy())
+    with pytest.raises(rtm.RTMError, match="stream 0"):
+        ctx.decompress(bad, stride, 2, 40, 40, y)
+    ctx.decompress(good, stride, 2, 40, 40, y)  # the context is still usable
+    assert np.array_equal(y.cpu().numpy()[1], oracle.codec_decompress(
+        oracle.codec_compress(x[2], 1e-3), 40, 40))
