@@ -52,7 +52,8 @@ def parse():
     p.add_argument("--shots", type=int, default=96)
     p.add_argument("--nt", type=int, default=5000)
     # other workloads of the method, each printing its own JSON line
-    p.add_argument("--workload", default="migrate", choices=["migrate", "ensemble", "serve"])
+    p.add_argument("--workload", default="migrate",
+                   choices=["migrate", "ensemble", "serve", "codec"])
     p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
@@ -483,6 +484,95 @@ def run_ensemble(args, local):
     ctx.close()
 
 
+def run_codec(args, local):
+    """Throughput and ratios of the device codec on the workflow's arrays
+    (§4.2, Tables 1-2): the survey's seismograms (96 x 5000 x 1701, modelled
+    with the true model), a 64-sample velocity ensemble and migrated images
+    (two samples' images, repeated to a batch of 64), at the paper's
+    tolerances (1e-4, 1e-1) and lossless.  Kernel time from CUDA events
+    around each codec launch; roofline bytes = floats read or written plus
+    stream bytes written or read."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = inputs.full_size(nshot=args.shots, nt=args.nt)
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    ens = inputs.ensemble(vm, s.dx, s.dz, 64).astype(np.float32)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    ctx = rtm.Context(local)
+    seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
+    ctx.model(grid, torch.from_numpy(s.vel.astype(np.float32)).to(dev), acq, -1, seis)
+    vels = torch.from_numpy(ens).to(dev)
+    two = torch.empty((2, s.nz, s.nx), dtype=torch.float32, device=dev)
+    ctx.migrate_ensemble(grid, vels[:2].contiguous(), acq, seis, rtm.Opts(4, rtm.SNAP_F16, 1e-6, 1),
+                         two)
+    imgs = two.repeat(32, 1, 1).contiguous()
+    torch.cuda.synchronize()
+    peak, peak_kind = measured_peaks()
+    paper = {  # Tables 1-2 (Marmousi2 files, MB): context only
+        ("velocity", 0.0): 4.78 / 6.10, ("velocity", 1e-4): 4.77 / 6.10,
+        ("velocity", 1e-1): 2.98 / 6.10, ("image", 0.0): 5.34 / 6.10,
+        ("image", 1e-4): 3.65 / 6.10, ("image", 1e-1): 1.83 / 6.10,
+        ("seismogram", 0.0): (48.46 / 76.20, 59.28 / 76.20),
+        ("seismogram", 1e-4): (8.38 / 76.20, 13.38 / 76.20)}
+    cases = []
+    clocks = Clocks(local)
+    clocks.start()
+    for kind, arr, tols in (("seismogram", seis, (1e-4, 0.0)), ("image", imgs, (1e-1, 1e-4, 0.0)),
+                            ("velocity", vels, (1e-1, 1e-4, 0.0))):
+        count, n0, n1 = arr.shape
+        raw = arr.numel() * 4
+        stride = (rtm.compress_bound(n0, n1) + 15) // 16 * 16
+        out = torch.empty(count * stride, dtype=torch.uint8, device=dev)
+        dec = torch.empty_like(arr)
+        for tol in tols:
+            for _ in range(args.warmup):
+                _, _, sizes = ctx.compress(arr, tol, out, stride)
+                ctx.decompress(out, stride, count, n0, n1, dec)
+            torch.cuda.synchronize()
+            ctx.set_profiling(True)
+            ctx.stats(reset=True)
+            for _ in range(args.steps):
+                _, _, sizes = ctx.compress(arr, tol, out, stride)
+            enc = ctx.stats(reset=True)
+            for _ in range(args.steps):
+                ctx.decompress(out, stride, count, n0, n1, dec)
+            decs = ctx.stats(reset=True)
+            ctx.set_profiling(False)
+            err = float((dec - arr).abs().max()) if tol > 0 else None
+            exact = bool(torch.equal(dec.view(torch.int32), arr.view(torch.int32))) if tol == 0 \
+                else None
+            comp = float(sum(sizes))
+            frac = comp / raw
+            enc_s = enc["codec_ms"] / 1e3 / args.steps
+            dec_s = decs["codec_ms"] / 1e3 / args.steps
+            c = {"array": kind, "shape": [count, n0, n1], "tol": tol,
+                 "size_frac": frac, "ratio": raw / comp,
+                 "paper_size_frac": paper.get((kind, tol)),
+                 "compress_gbs": raw / enc_s / 1e9, "decompress_gbs": raw / dec_s / 1e9,
+                 "compress_roofline_frac": (raw + comp) / enc_s / 1e9 / peak,
+                 "decompress_roofline_frac": (raw + comp) / dec_s / 1e9 / peak,
+                 "max_abs_err": err, "lossless_exact": exact}
+            cases.append(c)
+    ck = clocks.stop()
+    head = cases[0]
+    line = {
+        "workload": f"codec_seis{s.nshot}x{s.nt}x{s.nrec}_img64_vel64",
+        "metric": "codec GB/s of float data (compress) at the paper's tolerances",
+        "value": head["compress_gbs"], "unit": "GB/s", "steps": args.steps,
+        "warmup": args.warmup, "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
+        "l2": "inputs larger than L2 (3.3 GB of seismograms; 153 MB of images, velocities)",
+        "cases": cases, "clocks": ck, "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -492,6 +582,8 @@ def main():
         run_serve(args, local)
     elif args.workload == "ensemble":
         run_ensemble(args, local)
+    elif args.workload == "codec":
+        run_codec(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:
