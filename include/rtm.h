@@ -300,8 +300,8 @@ uint64_t rtm_compress_bound(long long n0, long long n1);
  * rtm_compress_bound(n0, n1), a multiple of 16; out 16-byte aligned) and its
  * byte count to out_bytes[i] (host).  An array holding a NaN or an infinity
  * cannot be coded with tol > 0: its out_bytes is 0 and the call returns
- * RTM_ERR_ARG after coding the others.  RTM_ERR_TIMEOUT if a device-side
- * wait gave up (nothing usable is written then). */
+ * RTM_ERR_ARG after coding the others.  Device scratch of about
+ * 1.25 x the input is taken from the context's pool for the call. */
 int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0, long long n1,
                  double tol, void *out, uint64_t out_stride, uint64_t *out_bytes,
                  void *stream);

@@ -20,14 +20,21 @@
 // below the plane where it entered the prefix (lowest first) and its sign.
 // kmin is the largest k >= 1 with 16 2^k + 21.5 <= tol 2^(28-e), else 0.
 //
-// Encoding: one warp per chunk, one lane per block.  Each lane computes its
-// block's coded length in closed form (events of the plane scan are the
-// suffix maxima of the coefficients' top planes), a warp scan places the
-// blocks, the lanes write their bits into shared memory, and each tile of 8
-// chunks finds its place in the output by a single-pass decoupled look-back
-// over the tiles before it (dynamic tile order, so every wait is on a tile
-// that is already running; each wait is bounded by the global timer).
-// Decoding: one thread per chunk, the chunk index giving its start.
+// Encoding, in three passes with no device-side waiting:
+//   1. one CTA per tile of 256 blocks (8 chunks), one warp per chunk, one lane
+//      per block.  Each lane computes its block's coded length in closed form
+//      (the events of the plane scan are the suffix maxima of the
+//      coefficients' top planes), a warp scan places the blocks, the lanes
+//      write their bits into shared memory, and the tile is copied to a
+//      staging slot of the maximum tile size;
+//   2. per array, an exclusive scan of the tiles' word counts, the header and
+//      the stream's byte count;
+//   3. one CTA per tile copies its words to their offset and writes the
+//      offsets of its chunks.
+// Decoding: a warp owns 32 chunks; each lane first walks one chunk to find
+// the bit offset of each of its blocks, then the warp decodes the chunks one
+// at a time, one block per lane, from the chunk's words staged in shared
+// memory, with coalesced stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,15 +53,15 @@ using u64 = unsigned long long;
 
 constexpr int kP = 28;
 constexpr int kChunk = 32;               // blocks per chunk = lanes of a warp
-constexpr int kWarps = 8;                // chunks per tile
-constexpr int kTile = kChunk * kWarps;   // blocks per tile (one CTA)
+constexpr int kWarps = 8;                // chunks per encoder tile
+constexpr int kTile = kChunk * kWarps;   // blocks per encoder tile (one CTA)
 constexpr int kBlockWords = 20;          // 640 bits bound one coded block
+constexpr int kChunkWords = kChunk * kBlockWords;
+constexpr int kTileWords = kTile * kBlockWords;
+constexpr int kDecWarps = 4;             // decoder: warps per CTA, 32 chunks per warp
 constexpr int kHeader = 64;
 constexpr u32 kMagic = 0x5A4D5452u;
 constexpr int kTab = 288;                // kmin by e + 150, e in [-150, 137]
-constexpr u64 kAgg = 1ull << 62, kIncl = 2ull << 62, kNonFinite = 1ull << 61,
-              kPoison = 1ull << 60, kValMask = (1ull << 40) - 1;
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 __host__ __device__ constexpr int perm(int i) {
   // coefficient (row*4 + col) in coding order: by lev(row) + lev(col),
@@ -66,42 +73,47 @@ __host__ __device__ constexpr int perm(int i) {
 
 struct EncArgs {
   const float *data;
-  long long n0, n1, nb1, nb, tiles, nchunk;
+  long long n0, n1;
+  u32 nb1, nb, tiles, nchunk;
   unsigned char *out;
   u64 stride, index_bytes;
-  u64 *sizes;
-  u64 *status;
-  u64 *ticket;
-  int *err;
+  u64 *sizes;             // [count] stream bytes
+  u32 *stage;             // [count * tiles][kTileWords] coded tiles
+  u32 *chunk_words;       // [count * tiles][kWarps]
+  u64 *tile_off;          // [count * tiles] word offset of each tile
+  u32 *nonfinite;         // [count] array holds a NaN or an infinity
+  const unsigned char *kmin;  // [kTab]
   double tol;
 };
 
 struct DecArgs {
   const unsigned char *in;
   float *out;
-  long long n0, n1, nb1, nb, nchunk;
+  long long n0, n1;
+  u32 nb1, nb, nchunk;
   u64 stride, index_bytes;
+  const unsigned char *kmin;  // [count][kTab]
   int *err;  // [0] malformed flag, [1] first malformed array
 };
 
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // kmin for every block exponent of a tolerance: the largest k in [1, 30]
 // with 16 2^k <= T - 21.5, T = tol 2^(28 - e), else 0.  T - 21.5 is exact
-// for T < 2^52, and above that k is 30 whatever the rounding.
-__device__ void fill_kmin(unsigned char *tab, double tol) {
-  for (int i = threadIdx.x; i < kTab; i += blockDim.x) {
+// for T < 2^52, and above that k is 30 whatever the rounding.  One CTA per
+// array, one thread per exponent; the tolerance comes from the stream header
+// (decoding) or from tol (encoding, in == nullptr).
+__global__ void k_cz_kmin(const unsigned char *in, u64 stride, double tol, unsigned char *tab) {
+  if (in) tol = *reinterpret_cast<const double *>(in + blockIdx.x * stride + 32);
+  const int i = threadIdx.x;
+  if (i >= kTab) return;
+  int k = 0;
+  if (tol > 0.0 && tol < 1e300) {
     const double r = ldexp(tol, kP - (i - 150)) - 21.5;
-    const int k = r >= 32.0 ? ilogb(r) - 4 : 0;
-    tab[i] = (unsigned char)min(k, 30);
+    k = r >= 32.0 ? ilogb(r) - 4 : 0;
   }
+  tab[blockIdx.x * kTab + i] = (unsigned char)min(k, 30);
 }
 
-// rint(x 2^(28 - e)) from the float's bits, for |x| < 2^e
+// rint(x 2^(28 - e)) from the float's bits, for |x| < 2^e (any e)
 __device__ __forceinline__ int fixed_point(u32 bits, int e) {
   const u32 E = (bits >> 23) & 0xffu;
   const u32 M = (bits & 0x7fffffu) | (E ? 0x800000u : 0u);
@@ -127,8 +139,8 @@ __device__ __forceinline__ u64 rne_shift(u64 a, int r) {
   return q + ((rem > half) | ((rem == half) & (q & 1ull)));
 }
 
-// q 2^(e - 28) rounded once to float (nearest, ties to even)
-__device__ __forceinline__ float fixed_to_float(long long q, int e) {
+// q 2^(e - 28) rounded once to float (nearest, ties to even), any e
+__device__ __forceinline__ float fixed_to_float_slow(long long q, int e) {
   if (q == 0) return 0.0f;
   const u32 sign = q < 0 ? 0x80000000u : 0u;
   const u64 a = q < 0 ? (u64)(-q) : (u64)q;
@@ -151,174 +163,198 @@ __device__ __forceinline__ float fixed_to_float(long long q, int e) {
 
 // ---------------------------------------------------------------- encode --
 
-// Magnitudes and signs of one block's coefficients in coding order, its
-// coded length, and what emission needs.
-template <bool LL>
-struct Coded {
-  using U = typename std::conditional<LL, u64, u32>::type;
-  U m[16];
-  u32 neg = 0;   // bit i: coefficient i negative
-  int top[16];   // highest set plane, -1 for zero
-  int s[16];     // plane at which coefficient i entered the prefix
-  int kmin = 0, e = 0, cur = 0, len = 1;
-  bool zero = true, nonfinite = false;
+// Bits appended at a running position of a zeroed shared-memory chunk: a
+// 64-bit accumulator whose whole words are OR-ed into place (the first and
+// last word of a block are shared with its neighbours).
+struct BitWriter {
+  u32 *buf;
+  u32 w;
+  int n;
+  u64 acc;
+  __device__ __forceinline__ BitWriter(u32 *b, u32 pos) : buf(b), w(pos >> 5), n(pos & 31), acc(0) {}
+  // v < 2^k, k <= 32
+  __device__ __forceinline__ void put(u64 v, int k) {
+    acc |= v << n;
+    n += k;
+    if (n >= 32) {
+      if ((u32)acc) atomicOr(buf + w, (u32)acc);
+      acc >>= 32;
+      n -= 32;
+      w++;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if ((u32)acc) atomicOr(buf + w, (u32)acc);
+  }
 };
 
+// One block: analysis (coded length) and emission.
 template <bool LL>
-__device__ __forceinline__ void analyse(const float (&x)[16], const unsigned char *ktab,
-                                        Coded<LL> &c) {
-  constexpr int Ktop = LL ? 32 : 30;
-  u32 bits[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) bits[i] = __float_as_uint(x[i]);
+struct Block {
   using S = typename std::conditional<LL, long long, int>::type;
-  S q[16];
-  if (LL) {
-    u32 any = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      any |= bits[i];
-      q[i] = (bits[i] >> 31) ? (S)(-1ll - (long long)(bits[i] & 0x7fffffffu)) : (S)bits[i];
-    }
-    if (!any) return;
-  } else {
-    u32 mx = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) mx = max(mx, bits[i] & 0x7fffffffu);
-    if (!mx) return;
-    c.nonfinite = mx >= 0x7f800000u;
-    const u32 E = mx >> 23;
-    c.e = E ? (int)E - 126 : (31 - __clz(mx)) - 148;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) q[i] = fixed_point(bits[i], c.e);
-    c.kmin = ktab[c.e + 150];
-  }
-  c.zero = false;
-  // two-level S-transform: rows, then columns (floor(d/2) = d >> 1)
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int o = pass ? l : 4 * l, st = pass ? 4 : 1;
-      const S a = q[o], b = q[o + st], cc = q[o + 2 * st], d = q[o + 3 * st];
-      const S d1 = b - a, s1 = a + (d1 >> 1);
-      const S d2 = d - cc, s2 = cc + (d2 >> 1);
-      const S dd = s2 - s1, ss = s1 + (dd >> 1);
-      q[o] = ss;
-      q[o + st] = dd;
-      q[o + 2 * st] = d1;
-      q[o + 3 * st] = d2;
-    }
-  }
-  int sfx = -1;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const S v = q[perm(i)];
-    c.neg |= (v < 0 ? 1u : 0u) << i;
-    c.m[i] = (typename Coded<LL>::U)(v < 0 ? -v : v);
-    if (LL)
-      c.top[i] = c.m[i] ? 63 - __clzll((long long)c.m[i]) : -1;
-    else
-      c.top[i] = c.m[i] ? 31 - __clz((int)c.m[i]) : -1;
-  }
-#pragma unroll
-  for (int i = 15; i >= 0; --i) {
-    sfx = max(sfx, c.top[i]);
-    c.s[i] = sfx;
-  }
-  // prefix members: s >= kmin; events (found coefficients): top == s
-  int cur = 0, nev = 0, refine = 0, plast = 0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (c.s[i] >= c.kmin) {
-      cur = i + 1;
-      plast = c.s[i];
-      nev += c.top[i] == c.s[i];
-      refine += c.s[i] - c.kmin + ((c.m[i] >> c.kmin) != 0);
-    }
-  }
-  c.cur = cur;
-  int sig;
-  if (cur == 0) {
-    sig = Ktop - c.kmin + 1;
-  } else {
-    sig = nev + cur + (Ktop - plast) + (cur < 16 ? plast - c.kmin + 1 : 0);
-  }
-  c.len = 1 + (LL ? 0 : 9) + sig + refine;
-}
+  using U = typename std::conditional<LL, u64, u32>::type;
+  static constexpr int Ktop = LL ? 32 : 30;
+  U m[16];
+  int s[16];      // plane at which coefficient i entered the prefix
+  u32 neg = 0;    // bit i: coefficient i negative
+  u32 ev = 0;     // bit i: coefficient i found by a scan (its top plane is s[i])
+  u32 nz = 0;     // bit i: kept magnitude of coefficient i is not zero
+  int kmin = 0, e = 0, cur = 0, len = 1;
+  bool zero = true, nonfinite = false;
 
-__device__ __forceinline__ void put(u32 *buf, u32 pos, u64 v) {
-  if (!v) return;
-  const u64 x = v << (pos & 31);
-  atomicOr(buf + (pos >> 5), (u32)x);
-  if (x >> 32) atomicOr(buf + (pos >> 5) + 1, (u32)(x >> 32));
-}
-
-template <bool LL>
-__device__ __forceinline__ void emit(const Coded<LL> &c, u32 *buf, u32 pos) {
-  constexpr int Ktop = LL ? 32 : 30;
-  if (c.zero) return;  // the flag bit is 0
-  put(buf, pos, 1);
-  pos += 1;
-  if (!LL) {
-    put(buf, pos, (u64)(c.e + 150));
-    pos += 9;
-  }
-  int k = Ktop, nxt = 0;
+  __device__ __forceinline__ void analyse(const u32 (&bits)[16], const unsigned char *ktab) {
+    S q[16];
+    if (LL) {
+      u32 any = 0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (c.s[i] >= c.kmin && c.top[i] == c.s[i]) {
-      pos += k - c.s[i];   // failed group tests of the planes in between
-      put(buf, pos, 1);    // group test succeeds
-      pos += 1 + (i - nxt);  // scanned coefficients without the bit
-      put(buf, pos, 1);    // the coefficient found
-      pos += 1;
-      nxt = i + 1;
-      k = c.s[i];
-    }
-  }
-  if (c.cur < 16) pos += k - c.kmin + 1;
+      for (int i = 0; i < 16; ++i) {
+        any |= bits[i];
+        q[i] = (bits[i] >> 31) ? (S)(-1ll - (long long)(bits[i] & 0x7fffffffu)) : (S)bits[i];
+      }
+      if (!any) return;
+    } else {
+      u32 mx = 0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (i < c.cur) {
-      const int w = c.s[i] - c.kmin;
-      const u64 t = (u64)(c.m[i] >> c.kmin);
-      put(buf, pos, t & ((1ull << w) - 1ull));
-      pos += w;
-      if (t) {
-        put(buf, pos, (c.neg >> i) & 1u);
-        pos += 1;
+      for (int i = 0; i < 16; ++i) mx = max(mx, bits[i] & 0x7fffffffu);
+      if (!mx) return;
+      nonfinite = mx >= 0x7f800000u;
+      const u32 E = mx >> 23;
+      e = E ? (int)E - 126 : (31 - __clz(mx)) - 148;
+      kmin = ktab[e + 150];
+      if (nonfinite) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) q[i] = 0;  // refused later; keep the length bounded
+      } else if (e >= -99) {
+        // x 2^(28-e) is exact (or below 1/2 when it underflows), 2^(28-e) a float
+        const float scale = __uint_as_float((u32)(28 - e + 127) << 23);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) q[i] = __float2int_rn(__fmul_rn(__uint_as_float(bits[i]), scale));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) q[i] = fixed_point(bits[i], e);
       }
     }
+    zero = false;
+    // two-level S-transform: rows, then columns (floor(d/2) = d >> 1)
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int o = pass ? l : 4 * l, st = pass ? 4 : 1;
+        const S a = q[o], b = q[o + st], cc = q[o + 2 * st], d = q[o + 3 * st];
+        const S d1 = b - a, s1 = a + (d1 >> 1);
+        const S d2 = d - cc, s2 = cc + (d2 >> 1);
+        const S dd = s2 - s1, ss = s1 + (dd >> 1);
+        q[o] = ss;
+        q[o + st] = dd;
+        q[o + 2 * st] = d1;
+        q[o + 3 * st] = d2;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const S v = q[perm(i)];
+      neg |= (v < 0 ? 1u : 0u) << i;
+      m[i] = (U)(v < 0 ? -v : v);
+    }
+    int sfx = -1;
+#pragma unroll
+    for (int i = 15; i >= 0; --i) {
+      const int top = LL ? 63 - __clzll((long long)m[i]) : 31 - __clz((int)m[i]);  // -1 for 0
+      sfx = max(sfx, top);
+      s[i] = sfx;
+      ev |= (u32)(top == sfx && top >= kmin) << i;
+      nz |= (u32)(top >= kmin) << i;
+    }
+    // prefix members: s >= kmin (a prefix, as s does not increase)
+    int refine = 0, plast = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const bool mem = s[i] >= kmin;
+      cur += mem;
+      refine += mem ? s[i] - kmin : 0;
+      plast = mem ? s[i] : plast;
+    }
+    refine += __popc(nz);
+    const int nev = __popc(ev);
+    const int sig = cur == 0 ? Ktop - kmin + 1
+                             : nev + cur + (Ktop - plast) + (cur < 16 ? plast - kmin + 1 : 0);
+    len = 1 + (LL ? 0 : 9) + sig + refine;
   }
-}
 
+  __device__ __forceinline__ void emit(u32 *buf, u32 pos) const {
+    if (zero) return;  // the flag bit is 0
+    BitWriter bw(buf, pos);
+    if (LL)
+      bw.put(1, 1);
+    else
+      bw.put(1u | ((u32)(e + 150) << 1), 10);
+    int k = Ktop, nxt = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if ((ev >> i) & 1u) {
+        bw.put(0, k - s[i]);  // failed group tests of the planes in between
+        const int gap = i - nxt;  // scanned coefficients without the bit
+        bw.put(1u | (1u << (gap + 1)), gap + 2);
+        nxt = i + 1;
+        k = s[i];
+      }
+    }
+    if (cur < 16) {
+      const int z = k - kmin + 1;  // up to 33
+      bw.put(0, z - (z > 32));
+      if (z > 32) bw.put(0, 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < cur) {
+        const int w = s[i] - kmin;
+        const u64 t = (u64)(m[i] >> kmin);
+        const u64 field = t & ((1ull << w) - 1ull);
+        const u64 sg = (neg >> i) & 1u;
+        if (LL) {
+          bw.put(field, w);
+          if ((nz >> i) & 1u) bw.put(sg, 1);
+        } else if ((nz >> i) & 1u) {
+          bw.put(field | (sg << w), w + 1);
+        } else {
+          bw.put(0, w);
+        }
+      }
+    }
+    bw.flush();
+  }
+};
+
+// Pass 1: code one tile (256 blocks, 8 chunks) into its staging slot of
+// kTileWords words and record the words of each chunk.
 template <bool LL>
-__global__ void __launch_bounds__(kTile) k_cz_encode(const EncArgs a) {
-  __shared__ u32 sbuf[kWarps][kChunk * kBlockWords];
+__global__ void __launch_bounds__(kTile, LL ? 2 : 3) k_cz_encode(const __grid_constant__ EncArgs a) {
+  __shared__ u32 sbuf[kWarps][kChunkWords];
   __shared__ u32 s_words[kWarps];
   __shared__ unsigned char s_kmin[kTab];
-  __shared__ u64 s_tile, s_prefix;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1ull);
-  if (!LL) fill_kmin(s_kmin, a.tol);
+  for (int i = threadIdx.x; i < kTab; i += blockDim.x) s_kmin[i] = a.kmin[i];
   __syncthreads();
-  const long long T = (long long)s_tile;
-  const long long arr = T / a.tiles, lt = T % a.tiles;
-  const long long b = lt * kTile + threadIdx.x;
-  const float *src = a.data + arr * a.n0 * a.n1;
+  const u64 T = blockIdx.x;  // tile over all arrays
+  const u32 arr = (u32)(T / a.tiles), lt = (u32)(T % a.tiles);
+  const u32 b = lt * kTile + threadIdx.x;
+  const float *src = a.data + (long long)arr * a.n0 * a.n1;
 
-  Coded<LL> c;
+  Block<LL> c;
   if (b < a.nb) {
-    const long long bi = b / a.nb1, bj = b % a.nb1;
-    float x[16];
+    const u32 bi = b / a.nb1, bj = b - bi * a.nb1;
+    u32 bits[16];
+    long long col[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) col[cc] = min((long long)(4 * bj + cc), a.n1 - 1);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const float *row = src + min(4 * bi + r, a.n0 - 1) * a.n1;
+      const float *row = src + min((long long)(4 * bi + r), a.n0 - 1) * a.n1;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) x[4 * r + cc] = row[min(4 * bj + cc, a.n1 - 1)];
+      for (int cc = 0; cc < 4; ++cc) bits[4 * r + cc] = __float_as_uint(row[col[cc]]);
     }
-    analyse<LL>(x, s_kmin, c);
+    c.analyse(bits, s_kmin);
   } else {
     c.len = 0;
   }
@@ -333,72 +369,62 @@ __global__ void __launch_bounds__(kTile) k_cz_encode(const EncArgs a) {
   const u32 nw = (u32)(chunk_bits + 31) >> 5;
   u32 *buf = sbuf[warp];
   for (u32 i = lane; i < nw; i += 32) buf[i] = 0;
-  __syncwarp();
-  if (c.len) emit<LL>(c, buf, (u32)(incl - c.len));
-  __syncwarp();
   if (lane == 0) s_words[warp] = nw;
+  __syncwarp();
+  if (c.len) c.emit(buf, (u32)(incl - c.len));
   const int nf = __syncthreads_or(c.nonfinite);
+  u32 off = 0;
+  for (int w = 0; w < warp; ++w) off += s_words[w];
+  u32 *stage = a.stage + T * kTileWords;
+  for (u32 i = lane; i < nw; i += 32) stage[off + i] = buf[i];
+  if (lane == 0) a.chunk_words[T * kWarps + warp] = nw;
+  if (threadIdx.x == 0 && nf) atomicOr(a.nonfinite + arr, 1u);
+}
 
-  // words before this tile: decoupled look-back over the array's tiles
-  if (warp == 0) {
-    u32 agg = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) agg += s_words[w];
-    const u64 mine = (u64)agg | (nf ? kNonFinite : 0ull);
-    volatile u64 *st = a.status + arr * a.tiles;
-    if (lane == 0) st[lt] = (lt == 0 ? kIncl : kAgg) | mine;
-    u64 prefix = 0, flags = 0;
-    if (lt > 0) {
-      long long j = lt - 1;
-      const unsigned long long t0 = now_ns();
-      for (;;) {
-        const long long idx = j - lane;
-        const u64 s = idx >= 0 ? (u64)st[idx] : (u64)kIncl;
-        const u32 notready = __ballot_sync(0xffffffffu, (s >> 62) == 0);
-        const u32 inc = __ballot_sync(0xffffffffu, (s >> 62) == 2);
-        const u32 need = inc ? (u32)(((u64)(inc & (0u - inc)) << 1) - 1ull) : 0xffffffffu;
-        if (notready & need) {
-          if (now_ns() - t0 > kWaitNs) {
-            flags |= kPoison;
-            if (lane == 0) atomicExch(a.err, 1);
-            break;
-          }
-          continue;
-        }
-        const bool use = (need >> lane) & 1u;
-        u64 v = use ? (s & kValMask) : 0ull, f = use ? (s & (kNonFinite | kPoison)) : 0ull;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          v += __shfl_xor_sync(0xffffffffu, v, d);
-          f |= __shfl_xor_sync(0xffffffffu, f, d);
-        }
-        prefix += v;
-        flags |= f;
-        if (inc) break;
-        j -= 32;
-      }
-      if (lane == 0) st[lt] = kIncl | ((prefix + agg) & kValMask) | flags | (mine & kNonFinite);
-    }
-    if (lane == 0) s_prefix = prefix | (flags & ~kValMask) | (mine & kNonFinite);
-  }
+// Pass 2: per array, the word offset of every tile (exclusive scan of the
+// tiles' words), the header and the stream's byte count.
+template <bool LL>
+__global__ void __launch_bounds__(1024) k_cz_scan(const __grid_constant__ EncArgs a) {
+  __shared__ u32 s_warp[32];
+  __shared__ u64 s_carry;
+  const u32 arr = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  const u64 pre = s_prefix;
-  if (pre & kPoison) return;  // a wait gave up: nothing is written
-  unsigned char *slot = a.out + arr * a.stride;
-  u32 *index = reinterpret_cast<u32 *>(slot + kHeader);
-  u32 *words = reinterpret_cast<u32 *>(slot + kHeader + a.index_bytes);
-  u64 start = pre & kValMask;
-  for (int w = 0; w < warp; ++w) start += s_words[w];
-  const long long chunk = lt * kWarps + warp;
-  if (chunk < a.nchunk) {
-    if (lane == 0) index[chunk] = (u32)start;
-    for (u32 i = lane; i < nw; i += 32) words[start + i] = buf[i];
+  const u32 *cw = a.chunk_words + (u64)arr * a.tiles * kWarps;
+  u64 *toff = a.tile_off + (u64)arr * a.tiles;
+  for (u32 base = 0; base < a.tiles; base += blockDim.x) {
+    const u32 t = base + threadIdx.x;
+    u32 v = 0;
+    if (t < a.tiles) {
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) v += cw[(u64)t * kWarps + w];
+    }
+    u32 incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const u32 y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    u32 before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      before += w < warp ? s_warp[w] : 0u;
+      total += s_warp[w];
+    }
+    const u64 carry = s_carry;
+    if (t < a.tiles) toff[t] = carry + before + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + total;
+    __syncthreads();
   }
-  if (lt == a.tiles - 1 && threadIdx.x == 0) {
-    u64 total = start;
-    for (int w = warp; w < kWarps; ++w) total += s_words[w];
-    const bool bad = (pre & kNonFinite) && !LL;
-    for (long long i = a.nchunk; i < (long long)(a.index_bytes / 4); ++i) index[i] = 0;
+  if (threadIdx.x == 0) {
+    const u64 words = s_carry;
+    unsigned char *slot = a.out + (u64)arr * a.stride;
+    const bool bad = !LL && a.nonfinite[arr];
+    u32 *index = reinterpret_cast<u32 *>(slot + kHeader);
+    for (u32 i = a.nchunk; i < (u32)(a.index_bytes / 4); ++i) index[i] = 0;
     u32 *h = reinterpret_cast<u32 *>(slot);
     h[0] = bad ? 0u : kMagic;
     h[1] = 2u;
@@ -409,16 +435,40 @@ __global__ void __launch_bounds__(kTile) k_cz_encode(const EncArgs a) {
     hl[1] = a.n1;
     *reinterpret_cast<double *>(slot + 32) = LL ? 0.0 : a.tol;
     u64 *hu = reinterpret_cast<u64 *>(slot + 40);
-    hu[0] = total;
+    hu[0] = words;
     hu[1] = (u64)a.nchunk;
     hu[2] = 0;
-    a.sizes[arr] = bad ? 0ull : kHeader + a.index_bytes + 4 * total;
+    a.sizes[arr] = bad ? 0ull : kHeader + a.index_bytes + 4 * words;
+  }
+}
+
+// Pass 3: copy each tile's words from its staging slot to its offset and
+// write the offsets of its chunks.
+__global__ void __launch_bounds__(kTile) k_cz_place(const __grid_constant__ EncArgs a) {
+  const u64 T = blockIdx.x;
+  const u32 arr = (u32)(T / a.tiles), lt = (u32)(T % a.tiles);
+  const u32 *cw = a.chunk_words + T * kWarps;
+  u32 tw = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) tw += cw[w];
+  const u64 base = a.tile_off[T];
+  unsigned char *slot = a.out + (u64)arr * a.stride;
+  u32 *index = reinterpret_cast<u32 *>(slot + kHeader);
+  u32 *words = reinterpret_cast<u32 *>(slot + kHeader + a.index_bytes);
+  const u32 *stage = a.stage + T * kTileWords;
+  for (u32 i = threadIdx.x; i < tw; i += blockDim.x) words[base + i] = stage[i];
+  if (threadIdx.x < kWarps) {
+    const u32 chunk = lt * kWarps + threadIdx.x;
+    u32 off = 0;
+    for (int w = 0; w < (int)threadIdx.x; ++w) off += cw[w];
+    if (chunk < a.nchunk) index[chunk] = (u32)(base + off);
   }
 }
 
 // ---------------------------------------------------------------- decode --
 
-struct Reader {
+// Sequential reader over global words [.., end) of one chunk (phase 1).
+struct GReader {
   const u32 *w;
   u64 nw, widx, pos, end;
   u64 buf;
@@ -434,167 +484,277 @@ struct Reader {
     refill();
   }
   __device__ __forceinline__ void refill() {
-    while (avail <= 32) {
+    if (avail <= 32) {
       const u32 v = widx < nw ? __ldg(w + widx) : 0u;
       buf |= (u64)v << avail;
       avail += 32;
       widx++;
     }
   }
+  __device__ __forceinline__ u32 peek() const { return (u32)buf; }
   __device__ __forceinline__ void skip(int n) {  // n <= 32
     buf >>= n;
     avail -= n;
     pos += n;
     refill();
   }
-  __device__ __forceinline__ u32 get(int n) {  // n <= 32
-    const u32 v = n ? (u32)buf & (0xffffffffu >> (32 - n)) : 0u;
-    skip(n);
-    return v;
-  }
-  // zero bits before the next one, at most lim (which are consumed)
-  __device__ __forceinline__ int zeros(int lim) {
-    int z = 0;
-    while (z < lim) {
-      const u32 v = (u32)buf;
-      int c = v ? __ffs(v) - 1 : 32;
-      c = min(c, lim - z);
-      skip(c);
-      z += c;
-      if (c < 32) break;
-    }
-    return z;
-  }
   __device__ bool overrun() const { return pos > end; }
 };
 
-template <bool LL>
-__device__ __forceinline__ bool decode_block(Reader &rd, const unsigned char *ktab,
-                                             unsigned char *sfx, float (&x)[16]) {
+// Random-access reader over a chunk's words staged in shared memory (phase 2);
+// w[nw] and w[nw + 1] are zero, so reads past the end see zeros.
+struct SReader {
+  const u32 *w;
+  u32 nw, pos;
+  __device__ __forceinline__ u32 peek() const {
+    const u32 i = min(pos >> 5, nw);
+    return __funnelshift_r(w[i], w[i + 1], pos & 31);
+  }
+  __device__ __forceinline__ void skip(int n) { pos += n; }
+  __device__ bool overrun() const { return pos > nw * 32; }
+};
+
+template <class R>
+__device__ __forceinline__ u32 getbits(R &rd, int n) {  // n <= 32
+  const u32 v = n ? rd.peek() & (0xffffffffu >> (32 - n)) : 0u;
+  rd.skip(n);
+  return v;
+}
+
+// zero bits before the next one, at most lim (all consumed)
+template <class R>
+__device__ __forceinline__ int zeros(R &rd, int lim) {
+  int z = 0;
+  while (z < lim) {
+    const u32 v = rd.peek();
+    const int c = min(v ? __ffs(v) - 1 : 32, lim - z);
+    rd.skip(c);
+    z += c;
+    if (c < 32) break;
+  }
+  return z;
+}
+
+// Parse one block.  FULL: reconstruct it into x; else only move past it.
+// Returns false on a malformed block.
+template <bool LL, bool FULL, class R>
+__device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, unsigned char *sfx,
+                                            int sstride, float (&x)[16]) {
   constexpr int Ktop = LL ? 32 : 30;
-  if (!rd.get(1)) {
+  if (!getbits(rd, 1)) {
+    if (FULL) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) x[i] = 0.0f;
+      for (int i = 0; i < 16; ++i) x[i] = 0.0f;
+    }
     return true;
   }
   int e = 0, kmin = 0;
   if (!LL) {
-    const int eb = (int)rd.get(9);
+    const int eb = (int)getbits(rd, 9);
     if (eb >= kTab) return false;
     e = eb - 150;
     kmin = ktab[eb];
   }
-  // significance section
+  // significance section: per event, the failed group tests of the planes
+  // before it, the successful test, the scanned coefficients without the bit
+  // and the one found; sfx[p] keeps the plane of the event at p
   u32 found = 0;
   int n = 0, k = Ktop;
   while (k >= kmin && n < 16) {
     const int lim = k - kmin + 1;
-    const int z = rd.zeros(lim);  // failed group tests
-    if (z == lim) break;
-    k -= z;
-    rd.skip(1);  // the group test that succeeds
-    const int g = rd.zeros(16 - n);
-    if (g == 16 - n) return false;
-    rd.skip(1);
+    const u32 v = rd.peek();
+    const int z = v ? __ffs(v) - 1 : 32;
+    int g;
+    if (z < lim && z < 31) {
+      const u32 v2 = v >> (z + 1);  // 31 - z valid bits
+      g = v2 ? __ffs(v2) - 1 : 32;
+      if (g < 31 - z && g < 16 - n) {
+        rd.skip(z + g + 2);
+      } else {
+        rd.skip(z + 1);
+        g = zeros(rd, 16 - n);
+        if (g == 16 - n) return false;
+        rd.skip(1);
+      }
+      k -= z;
+    } else {
+      const int zz = zeros(rd, lim);
+      if (zz == lim) break;
+      k -= zz;
+      rd.skip(1);
+      g = zeros(rd, 16 - n);
+      if (g == 16 - n) return false;
+      rd.skip(1);
+    }
     const int p = n + g;
-    for (int i = n; i <= p; ++i) sfx[i * blockDim.x] = (unsigned char)k;
+    sfx[p * sstride] = (unsigned char)k;
     found |= 1u << p;
     n = p + 1;
   }
-  // refinement: magnitudes and signs, back in block order
-  using S = long long;
+  // refinement: magnitudes and signs
+  using S = typename std::conditional<LL, long long, int>::type;
   S q[16];
+  bool wide = false;  // fixed accuracy with kmin > 26 reconstructs in 64 bits
+  long long qw[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    S v = 0;
+    long long v = 0;
     if (i < n) {
-      const int w = sfx[i * blockDim.x] - kmin;
-      u64 t = w > 32 ? 0ull : (u64)rd.get(min(w, 32));
+      const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;  // plane of the next event
+      u64 t = w > 32 ? 0ull : (u64)getbits(rd, min(w, 32));
       if ((found >> i) & 1u) t |= 1ull << w;
       if (t) {
-        const bool ng = rd.get(1);
-        v = (S)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
+        const bool ng = getbits(rd, 1);
+        v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
         if (ng) v = -v;
       }
     }
-    q[perm(i)] = v;
-  }
-  // inverse transform: columns, then rows
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int o = pass ? 4 * l : l, st = pass ? 1 : 4;
-      const S ss = q[o], dd = q[o + st], d1 = q[o + 2 * st], d2 = q[o + 3 * st];
-      const S s1 = ss - (dd >> 1), s2 = dd + s1;
-      const S a0 = s1 - (d1 >> 1), b0 = d1 + a0;
-      const S c0 = s2 - (d2 >> 1), e0 = d2 + c0;
-      q[o] = a0;
-      q[o + st] = b0;
-      q[o + 2 * st] = c0;
-      q[o + 3 * st] = e0;
+    if (FULL) {
+      q[perm(i)] = (S)v;
+      qw[perm(i)] = v;
     }
   }
+  if (!FULL) return true;
+  if (!LL) wide = kmin > 26;
   bool ok = true;
+  if (LL || !wide) {
+    // inverse transform: columns, then rows
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (LL) {
-      ok &= q[i] >= -2147483648ll && q[i] <= 2147483647ll;
-      const u32 u = q[i] < 0 ? 0x80000000u | (u32)(-1ll - q[i]) : (u32)q[i];
-      x[i] = __uint_as_float(u);
-    } else {
-      x[i] = fixed_to_float(q[i], e);
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int o = pass ? 4 * l : l, st = pass ? 1 : 4;
+        const S ss = q[o], dd = q[o + st], d1 = q[o + 2 * st], d2 = q[o + 3 * st];
+        const S s1 = ss - (dd >> 1), s2 = dd + s1;
+        const S a0 = s1 - (d1 >> 1), b0 = d1 + a0;
+        const S c0 = s2 - (d2 >> 1), e0 = d2 + c0;
+        q[o] = a0;
+        q[o + st] = b0;
+        q[o + 2 * st] = c0;
+        q[o + 3 * st] = e0;
+      }
     }
+    if (LL) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const long long v = (long long)q[i];
+        ok &= v >= -2147483648ll && v <= 2147483647ll;
+        x[i] = __uint_as_float(v < 0 ? 0x80000000u | (u32)(-1ll - v) : (u32)v);
+      }
+    } else if (e >= -98 && e <= 120) {
+      // every nonzero value is a normal float: one rounding in the conversion,
+      // then an exact scaling by 2^(e-28)
+      const float scale = __uint_as_float((u32)(e - kP + 127) << 23);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = __fmul_rn(__int2float_rn((int)q[i]), scale);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[i] = fixed_to_float_slow((long long)q[i], e);
+    }
+  } else {
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int o = pass ? 4 * l : l, st = pass ? 1 : 4;
+        const long long ss = qw[o], dd = qw[o + st], d1 = qw[o + 2 * st], d2 = qw[o + 3 * st];
+        const long long s1 = ss - (dd >> 1), s2 = dd + s1;
+        const long long a0 = s1 - (d1 >> 1), b0 = d1 + a0;
+        const long long c0 = s2 - (d2 >> 1), e0 = d2 + c0;
+        qw[o] = a0;
+        qw[o + st] = b0;
+        qw[o + 2 * st] = c0;
+        qw[o + 3 * st] = e0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = fixed_to_float_slow(qw[i], e);
   }
   return ok;
 }
 
 template <bool LL>
-__device__ void decode_chunk(const DecArgs &a, const unsigned char *slot, long long arr,
-                             const unsigned char *ktab, unsigned char *sfx) {
-  const long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ch >= a.nchunk) return;
+__device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 arr,
+                             const unsigned char *ktab, u32 (*offs)[33], u32 *cw, u32 *cstart,
+                             u32 *cnw, unsigned char *sfx, bool &bad) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 g = blockIdx.x * kDecWarps + warp;  // this warp's group of 32 chunks
+  const u32 c0 = g * 32;
+  if (c0 >= a.nchunk) return;
   const u64 nwords = *reinterpret_cast<const u64 *>(slot + 40);
   const u32 *index = reinterpret_cast<const u32 *>(slot + kHeader);
   const u32 *words = reinterpret_cast<const u32 *>(slot + kHeader + a.index_bytes);
-  const u64 start = index[ch];
-  const u64 next = ch + 1 < a.nchunk ? (u64)index[ch + 1] : nwords;
-  bool ok = start <= next && next <= nwords && (ch > 0 || start == 0);
-  float *dst = a.out + arr * a.n0 * a.n1;
-  if (ok) {
-    Reader rd;
-    rd.init(words, next, start);
-    const long long b0 = ch * kChunk, b1 = min(b0 + kChunk, a.nb);
-    for (long long b = b0; b < b1 && ok; ++b) {
+  // phase 1: lane l finds the block offsets of chunk c0 + l
+  {
+    const u32 c = c0 + lane;
+    bool ok = true;
+    u32 start = 0, next = 0;
+    if (c < a.nchunk) {
+      start = index[c];
+      next = c + 1 < a.nchunk ? index[c + 1] : (u32)min(nwords, (u64)0xffffffffu);
+      ok = start <= next && next <= nwords && next - start <= (u32)kChunkWords &&
+           (c > 0 || start == 0);
+      if (ok) {
+        GReader rd;
+        rd.init(words, next, start);
+        const u32 b0 = c * kChunk, nblk = min((u32)kChunk, a.nb - b0);
+        float x[16];
+        for (u32 k = 0; k < nblk && ok; ++k) {
+          offs[lane][k] = (u32)(rd.pos - (u64)start * 32);
+          ok = parse_block<LL, false>(rd, ktab, sfx, kDecWarps * 32, x);
+        }
+        ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next;
+      }
+    }
+    cstart[lane] = start;
+    cnw[lane] = ok ? next - start : 0;
+    if (!ok) bad = true;
+  }
+  __syncwarp();
+  // phase 2: one chunk at a time, one block per lane, coalesced stores
+  float *dst = a.out + (long long)arr * a.n0 * a.n1;
+  for (int j = 0; j < 32; ++j) {
+    const u32 c = c0 + j;
+    if (c >= a.nchunk) break;
+    const u32 nw = cnw[j], st0 = cstart[j];
+    for (u32 i = lane; i < nw + 2; i += 32) cw[i] = i < nw ? __ldg(words + st0 + i) : 0u;
+    __syncwarp();
+    const u32 b = c * kChunk + lane;
+    if (nw && b < a.nb) {
+      SReader rd{cw, nw, offs[j][lane]};
       float x[16];
-      ok = decode_block<LL>(rd, ktab, sfx, x);
-      const long long bi = b / a.nb1, bj = b % a.nb1;
+      const bool ok = parse_block<LL, true>(rd, ktab, sfx, kDecWarps * 32, x) && !rd.overrun();
+      if (!ok) bad = true;
+      const u32 bi = b / a.nb1, bj = b - bi * a.nb1;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const long long i = 4 * bi + r;
+        const long long i = 4ll * bi + r;
         if (i < a.n0) {
+          float *row = dst + i * a.n1;
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
-            const long long j = 4 * bj + cc;
-            if (j < a.n1) dst[i * a.n1 + j] = x[4 * r + cc];
+            const long long jj = 4ll * bj + cc;
+            if (jj < a.n1) row[jj] = x[4 * r + cc];
           }
         }
       }
     }
-    ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next;
-  }
-  if (!ok) {
-    atomicExch(a.err, 1);
-    atomicMin(a.err + 1, (int)arr);
+    __syncwarp();
   }
 }
 
-__global__ void __launch_bounds__(128) k_cz_decode(const DecArgs a) {
+// One kernel per mode (smaller code per kernel); each skips the other mode's
+// streams, and the fixed-accuracy one reports bad headers.
+template <bool LL>
+__global__ void __launch_bounds__(kDecWarps * 32) k_cz_decode(const __grid_constant__ DecArgs a) {
+  __shared__ u32 s_offs[kDecWarps][32][33];
+  __shared__ u32 s_cw[kDecWarps][kChunkWords + 2];
+  __shared__ u32 s_start[kDecWarps][32], s_nw[kDecWarps][32];
+  __shared__ unsigned char s_sfx[16][kDecWarps * 32];
   __shared__ unsigned char s_kmin[kTab];
-  __shared__ unsigned char s_sfx[16 * 128];
   __shared__ int s_ok;
-  const long long arr = blockIdx.y;
-  const unsigned char *slot = a.in + arr * a.stride;
+  const u32 arr = blockIdx.y;
+  const unsigned char *slot = a.in + (u64)arr * a.stride;
   if (threadIdx.x == 0) {
     const u32 *h = reinterpret_cast<const u32 *>(slot);
     const long long *hl = reinterpret_cast<const long long *>(slot + 16);
@@ -605,22 +765,24 @@ __global__ void __launch_bounds__(128) k_cz_decode(const DecArgs a) {
            hl[0] == a.n0 && hl[1] == a.n1 && hu[1] == (u64)a.nchunk && hu[0] <= cap &&
            (h[2] ? tol == 0.0 : (tol > 0.0 && tol < 1e300));
   }
+  for (int i = threadIdx.x; i < kTab; i += blockDim.x) s_kmin[i] = a.kmin[arr * kTab + i];
   __syncthreads();
   if (!s_ok) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (!LL && threadIdx.x == 0 && blockIdx.x == 0) {
       atomicExch(a.err, 1);
       atomicMin(a.err + 1, (int)arr);
     }
     return;
   }
-  const double tol = *reinterpret_cast<const double *>(slot + 32);
-  const int mode = reinterpret_cast<const u32 *>(slot)[2];
-  if (!mode) fill_kmin(s_kmin, tol);
-  __syncthreads();
-  if (mode)
-    decode_chunk<true>(a, slot, arr, s_kmin, s_sfx + threadIdx.x);
-  else
-    decode_chunk<false>(a, slot, arr, s_kmin, s_sfx + threadIdx.x);
+  if ((reinterpret_cast<const u32 *>(slot)[2] != 0) != LL) return;
+  const int warp = threadIdx.x >> 5;
+  bool bad = false;
+  decode_group<LL>(a, slot, arr, s_kmin, s_offs[warp], s_cw[warp], s_start[warp], s_nw[warp],
+                   &s_sfx[0][threadIdx.x], bad);
+  if (bad) {
+    atomicExch(a.err, 1);
+    atomicMin(a.err + 1, (int)arr);
+  }
 }
 
 }  // namespace
@@ -644,53 +806,80 @@ bool codec_shape(long long n0, long long n1, long long *nb1, long long *nb, long
   return true;
 }
 
+// device scratch of one compression, in bytes
+u64 codec_scratch_bytes(long long count, long long n0, long long n1) {
+  long long nb = 0;
+  if (!codec_shape(n0, n1, nullptr, &nb, nullptr, nullptr, nullptr)) return 0;
+  const u64 tiles = (u64)count * (u64)((nb + kTile - 1) / kTile);
+  return tiles * (4ull * kTileWords + 4ull * kWarps + 8ull) + 4ull * (u64)count + 512;
+}
+
 cudaError_t launch_cz_encode(const float *data, long long count, long long n0, long long n1,
-                             double tol, unsigned char *out, u64 stride, u64 *sizes, u64 *scratch,
-                             int *err, cudaStream_t st) {
+                             double tol, unsigned char *out, u64 stride, u64 *sizes,
+                             unsigned char *scratch, cudaStream_t st) {
   EncArgs a{};
-  u64 bound = 0;
-  if (!codec_shape(n0, n1, &a.nb1, &a.nb, &a.nchunk, &a.index_bytes, &bound))
+  long long nb1, nb, nchunk;
+  if (!codec_shape(n0, n1, &nb1, &nb, &nchunk, &a.index_bytes, nullptr))
     return cudaErrorInvalidValue;
+  a.nb1 = (u32)nb1;
+  a.nb = (u32)nb;
+  a.nchunk = (u32)nchunk;
   a.data = data;
   a.n0 = n0;
   a.n1 = n1;
-  a.tiles = (a.nb + kTile - 1) / kTile;
+  a.tiles = (u32)((nb + kTile - 1) / kTile);
+  const u64 tiles = (u64)count * a.tiles;
+  if (tiles > 0x7fffffffull || count > 0xffffffffll) return cudaErrorInvalidValue;
   a.out = out;
   a.stride = stride;
   a.sizes = sizes;
-  a.ticket = scratch;
-  a.status = scratch + 1;
-  a.err = err;
+  // scratch: stage | tile_off | chunk_words | nonfinite | kmin; every word but
+  // the non-finite flags is written before it is read
+  a.stage = reinterpret_cast<u32 *>(scratch);
+  a.tile_off = reinterpret_cast<u64 *>(scratch + tiles * 4ull * kTileWords);
+  a.chunk_words = reinterpret_cast<u32 *>(scratch + tiles * (4ull * kTileWords + 8ull));
+  a.nonfinite = a.chunk_words + tiles * kWarps;
+  unsigned char *tab = reinterpret_cast<unsigned char *>(a.nonfinite + count);
+  a.kmin = tab;
   a.tol = tol;
-  const long long grid = count * a.tiles;
-  if (grid > 0x7fffffffll) return cudaErrorInvalidValue;
-  if (tol > 0)
-    k_cz_encode<false><<<(unsigned)grid, kTile, 0, st>>>(a);
-  else
-    k_cz_encode<true><<<(unsigned)grid, kTile, 0, st>>>(a);
+  cudaError_t e = cudaMemsetAsync(a.nonfinite, 0, 4ull * (u64)count, st);
+  if (e != cudaSuccess) return e;
+  k_cz_kmin<<<1, kTab, 0, st>>>(nullptr, 0, tol, tab);
+  if (tol > 0) {
+    k_cz_encode<false><<<(unsigned)tiles, kTile, 0, st>>>(a);
+    k_cz_scan<false><<<(unsigned)count, 1024, 0, st>>>(a);
+  } else {
+    k_cz_encode<true><<<(unsigned)tiles, kTile, 0, st>>>(a);
+    k_cz_scan<true><<<(unsigned)count, 1024, 0, st>>>(a);
+  }
+  k_cz_place<<<(unsigned)tiles, kTile, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-u64 codec_scratch_words(long long count, long long n0, long long n1) {
-  long long nb = 0;
-  if (!codec_shape(n0, n1, nullptr, &nb, nullptr, nullptr, nullptr)) return 0;
-  return 1 + (u64)count * (u64)((nb + kTile - 1) / kTile);
-}
-
+// kmin tables of the streams to decode: count x kTab bytes in tab
 cudaError_t launch_cz_decode(const unsigned char *in, u64 stride, long long count, long long n0,
-                             long long n1, float *out, int *err, cudaStream_t st) {
+                             long long n1, float *out, unsigned char *tab, int *err,
+                             cudaStream_t st) {
   DecArgs a{};
-  if (!codec_shape(n0, n1, &a.nb1, &a.nb, &a.nchunk, &a.index_bytes, nullptr))
+  long long nb1, nb, nchunk;
+  if (!codec_shape(n0, n1, &nb1, &nb, &nchunk, &a.index_bytes, nullptr))
     return cudaErrorInvalidValue;
+  a.nb1 = (u32)nb1;
+  a.nb = (u32)nb;
+  a.nchunk = (u32)nchunk;
   a.in = in;
   a.out = out;
   a.n0 = n0;
   a.n1 = n1;
   a.stride = stride;
+  a.kmin = tab;
   a.err = err;
-  if (count > 65535 || (a.nchunk + 127) / 128 > 0x7fffffffll) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((a.nchunk + 127) / 128), (unsigned)count);
-  k_cz_decode<<<grid, 128, 0, st>>>(a);
+  if (count > 65535) return cudaErrorInvalidValue;
+  const long long groups = (nchunk + 31) / 32;
+  const dim3 grid((unsigned)((groups + kDecWarps - 1) / kDecWarps), (unsigned)count);
+  k_cz_kmin<<<(unsigned)count, kTab, 0, st>>>(in, stride, 0.0, tab);
+  k_cz_decode<false><<<grid, kDecWarps * 32, 0, st>>>(a);
+  k_cz_decode<true><<<grid, kDecWarps * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -783,20 +972,17 @@ int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0,
     CZ_CU(dout.alloc(ctx, (size_t)count * out_stride, st));
     d_out = dout.as<unsigned char>();
   }
-  const u64 nw = codec_scratch_words(count, n0, n1);
-  const size_t sbytes = nw * 8 + (size_t)count * 8 + 16;
-  CZ_CU(scratch.alloc(ctx, sbytes, st));
-  CZ_CU(cudaMemsetAsync(scratch.p, 0, sbytes, st));
-  u64 *ticket = scratch.as<u64>();
-  u64 *sizes = ticket + nw;
-  int *err = reinterpret_cast<int *>(sizes + count);
+  const u64 stage_bytes = codec_scratch_bytes(count, n0, n1);
+  DevBuf dsizes;
+  CZ_CU(scratch.alloc(ctx, stage_bytes, st));
+  CZ_CU(dsizes.alloc(ctx, (size_t)count * 8, st));
+  u64 *sizes = dsizes.as<u64>();
   CodecTimer tm(ctx, st);
   tm.start();
-  CZ_CU(launch_cz_encode(d_data, count, n0, n1, tol, d_out, out_stride, sizes, ticket, err, st));
+  CZ_CU(launch_cz_encode(d_data, count, n0, n1, tol, d_out, out_stride, sizes,
+                         scratch.as<unsigned char>(), st));
   tm.stop();
-  int herr = 0;
   CZ_CU(cudaMemcpyAsync(out_bytes, sizes, (size_t)count * 8, cudaMemcpyDeviceToHost, st));
-  CZ_CU(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
   CZ_CU(cudaStreamSynchronize(st));
   double total = 0;
   long long bad = 0, first_bad = -1;
@@ -806,10 +992,6 @@ int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0,
     bad += !out_bytes[i];
   }
   tm.account((double)nbytes_in + total);
-  if (herr) {
-    for (long long i = 0; i < count; ++i) out_bytes[i] = 0;
-    return fail(ctx, RTM_ERR_TIMEOUT, "a device-side wait of the encoder gave up");
-  }
   if (!out_dev) {
     for (long long i = 0; i < count; ++i)
       if (out_bytes[i])
@@ -850,12 +1032,13 @@ int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long c
     CZ_CU(dout.alloc(ctx, nbytes_out, st));
     d_data = dout.as<float>();
   }
-  CZ_CU(scratch.alloc(ctx, 16, st));
+  CZ_CU(scratch.alloc(ctx, 16 + (size_t)count * kTab, st));
   const int init[4] = {0, 0x7fffffff, 0, 0};
   CZ_CU(cudaMemcpyAsync(scratch.p, init, 16, cudaMemcpyHostToDevice, st));
   CodecTimer tm(ctx, st);
   tm.start();
-  CZ_CU(launch_cz_decode(d_in, in_stride, count, n0, n1, d_data, scratch.as<int>(), st));
+  CZ_CU(launch_cz_decode(d_in, in_stride, count, n0, n1, d_data,
+                         scratch.as<unsigned char>() + 16, scratch.as<int>(), st));
   tm.stop();
   int herr[2] = {0, 0};
   CZ_CU(cudaMemcpyAsync(herr, scratch.p, 8, cudaMemcpyDeviceToHost, st));
