@@ -23,7 +23,8 @@ import numpy as np
 from .stats import ensemble_stats, uncertainty_maps  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "rtm_oracle.c"), os.path.join(_HERE, "codec_oracle.c")]
+_SRCS = [os.path.join(_HERE, "rtm_oracle.c"), os.path.join(_HERE, "codec_oracle.c"),
+         os.path.join(_HERE, "eikonal_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -88,6 +89,10 @@ def lib():
             L.oracle_codec_compress.restype = C.c_uint64
             L.oracle_codec_decompress.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
                                                   C.c_int64]
+            L.oracle_eikonal_update.argtypes = [C.c_double] * 5
+            L.oracle_eikonal_update.restype = C.c_double
+            L.oracle_eikonal.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_void_p,
+                                         C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -261,3 +266,27 @@ def codec_decompress(blob: bytes, n0, n1):
     if rc:
         raise ValueError(f"corrupt stream ({rc})")
     return out
+
+
+# -------------------------------------------------------------- eikonal --
+
+def eikonal_update(a, b, s, dz, dx) -> float:
+    """Upwind update of one node from its smaller vertical (a) and horizontal
+    (b) neighbour times."""
+    return float(lib().oracle_eikonal_update(float(a), float(b), float(s), float(dz), float(dx)))
+
+
+def eikonal(vel, dz, dx, src_iz, src_ix):
+    """First-arrival traveltimes [nz][nx] (FP64, fast marching) for velocity
+    vel [nz][nx] from the source nodes (src_iz[k], src_ix[k]), all at T = 0."""
+    v = np.ascontiguousarray(np.asarray(vel, np.float64))
+    nz, nx = v.shape
+    s = np.ascontiguousarray(1.0 / v)
+    iz, _ = _i(np.atleast_1d(src_iz))
+    ix, _ = _i(np.atleast_1d(src_ix))
+    T = np.empty((nz, nx))
+    rc = lib().oracle_eikonal(nz, nx, float(dz), float(dx), s.ctypes.data, iz.size,
+                              iz.ctypes.data, ix.ctypes.data, T.ctypes.data)
+    if rc:
+        raise ValueError("bad eikonal arguments")
+    return T
