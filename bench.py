@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--nt", type=int, default=5000)
     # other workloads of the method, each printing its own JSON line
     p.add_argument("--workload", default="migrate",
-                   choices=["migrate", "ensemble", "serve", "codec"])
+                   choices=["migrate", "ensemble", "serve", "codec", "eikonal"])
     p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
@@ -573,6 +573,89 @@ def run_codec(args, local):
     ctx.close()
 
 
+def run_eikonal(args, local):
+    """First-arrival traveltime panels of the tomography stage (§2.1 Eq. 1,
+    §3): the 17 km x 3.5 km layered/faulted model generated on a 40 m grid
+    (426 x 88), a velocity ensemble of --samples (default 64) samples, 34
+    surface sources every 480 m (the paper's 34 traveltime panels),
+    receivers at every surface node.  One step = one rtm_eikonal call over
+    the whole ensemble, timed with CUDA events; both field storages."""
+    import torch
+
+    import oracle
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nz, nx, h = 88, 426, 40.0
+    base = inputs.layered_faulted(nz, nx, h, h, seed=20010644)
+    ens = inputs.ensemble(base, h, h, args.samples).astype(np.float32)
+    src_ix = (6 + 12 * np.arange(34)).astype(np.int32)
+    src_iz = np.zeros(34, np.int32)
+    rec_ix = np.arange(nx, dtype=np.int32)
+    rec_iz = np.zeros(nx, np.int32)
+    ctx = rtm.Context(local)
+    vel = torch.from_numpy(ens).to(dev)
+    times = torch.empty((args.samples, 34, nx), dtype=torch.float32, device=dev)
+    solves = args.samples * 34
+    res = {}
+    clocks = Clocks(local)
+    clocks.start()
+    for offchip in (False, True):
+        for _ in range(args.warmup):
+            iters = ctx.eikonal(vel, h, h, src_iz, src_ix, rec_iz, rec_ix, times=times,
+                                offchip=offchip)
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        ctx.stats(reset=True)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            iters = ctx.eikonal(vel, h, h, src_iz, src_ix, rec_iz, rec_ix, times=times,
+                                offchip=offchip)
+        e1.record(st)
+        torch.cuda.synchronize()
+        stt = ctx.stats(reset=True)
+        ctx.set_profiling(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        kms = stt["eik_ms"] / args.steps
+        res["offchip" if offchip else "shared"] = {
+            "solves_per_s": solves / (ms / 1e3), "kernel_solves_per_s": solves / (kms / 1e3),
+            "ms_per_step": ms, "kernel_ms_per_step": kms,
+            "node_updates_per_s": stt["eik_updates"] / (stt["eik_ms"] / 1e3),
+            "iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters))}
+    ck = clocks.stop()
+    best = max(res, key=lambda k: res[k]["solves_per_s"])
+    # end to end with host buffers: velocities in, panels out
+    h_vel = torch.from_numpy(ens).pin_memory()
+    h_times = torch.empty((args.samples, 34, nx), dtype=torch.float32).pin_memory()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.eikonal(h_vel, h, h, src_iz, src_ix, rec_iz, rec_ix, times=h_times,
+                    offchip=best == "offchip")
+    e2e = solves * args.steps / (time.perf_counter() - t)
+    # the oracle (fast marching, FP64) on one sample's 34 sources
+    t = time.perf_counter()
+    for k in range(34):
+        oracle.eikonal(ens[0].astype(np.float64), h, h, 0, src_ix[k])
+    cpu_dt = time.perf_counter() - t
+    line = {
+        "workload": f"eikonal_426x88_40m_{args.samples}samples_34src",
+        "metric": "traveltime solves/s (one source x one velocity sample)",
+        "value": res[best]["solves_per_s"], "unit": "solves/s", "steps": args.steps,
+        "warmup": args.warmup, "storage": best, "variants": res,
+        "e2e": {"value": e2e, "unit": "solves/s",
+                "h2d_bytes_per_step": int(h_vel.numel() * 4),
+                "d2h_bytes_per_step": int(h_times.numel() * 4)},
+        "cpu_baseline": {"value": 34 / cpu_dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"34 fast-marching solves (FP64) of one sample, {cpu_dt:.2f} s"},
+        "clocks": ck, "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -584,6 +667,8 @@ def main():
         run_ensemble(args, local)
     elif args.workload == "codec":
         run_codec(args, local)
+    elif args.workload == "eikonal":
+        run_eikonal(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:

@@ -139,7 +139,9 @@ int rtm_ctx_set_batch(rtm_ctx *ctx, int max_items);
  * every kernel the library launched.  codec_ms and codec_bytes are the same
  * for the codec kernels of rtm_compress / rtm_decompress: device time of
  * each kernel, and its algorithmic bytes (the floats read or written plus
- * the stream bytes written or read). */
+ * the stream bytes written or read).  eik_ms and eik_updates are the device
+ * time of the traveltime solver launches of rtm_eikonal and the node updates
+ * they made (4 sweeps x nodes per iteration, the last one included). */
 typedef struct {
   long long step_launches;
   double step_ms;
@@ -150,6 +152,9 @@ typedef struct {
   long long codec_launches;
   double codec_ms;
   double codec_bytes;
+  long long eik_launches;
+  double eik_ms;
+  double eik_updates;
 } rtm_stats;
 
 /* Turn profiling on (1) or off (0).  With profiling on, every migration
@@ -314,6 +319,35 @@ int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0,
  * damaged chunks are then unspecified). */
 int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long count,
                    long long n0, long long n1, float *data, void *stream);
+
+/* ----------------------------------------------------------- eikonal --
+ * First-arrival traveltimes: the forward operator of the tomography stage
+ * (§2.1 Eq. 1: traveltimes of the proposed velocity model from the eikonal
+ * equation |grad T| = 1/v; §3: solved for every source at each sampler
+ * iteration, which dominates that stage).  The first-order upwind scheme on
+ * the nz x nx grid (spacings dz, dx in m): with a, b the smaller vertical and
+ * horizontal neighbour times, ((T-a)^+/dz)^2 + ((T-b)^+/dx)^2 = (1/v)^2, and
+ * T = 0 at the source node.  Its discrete solution is unique (the one fast
+ * marching computes); the device reaches it by parallel fast sweeping, one
+ * (sample, source) problem per CTA, in FP32.
+ * vel: [nsample][nz][nx] m/s, host or device, positive and finite
+ * (RTM_ERR_ARG otherwise).  Sources and receivers: host arrays of node
+ * indices.  times: [nsample][nsrc][nrec] s at the receivers, fields:
+ * [nsample][nsrc][nz][nx] s, either may be NULL but not both; host or device.
+ * flags: 0, or RTM_EIK_OFFCHIP to keep every problem's work field in an
+ * L2-resident device buffer even when it fits in shared memory (more
+ * problems per SM, each level of a sweep waiting on L2 instead of shared
+ * memory); fields larger than shared memory are always kept that way.
+ * max_iter (<= 0: 64) caps the iterations of four sweeps; iters (host,
+ * nullable, [nsample * nsrc]) receives the iterations each problem took to
+ * reach its fixed point (the last one changing nothing), -1 at the cap, in
+ * which case the call returns RTM_ERR_STATE after writing every output.
+ * Synchronises the stream. */
+#define RTM_EIK_OFFCHIP 1
+int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, int nsample,
+                const float *vel, int nsrc, const int *src_iz, const int *src_ix, int nrec,
+                const int *rec_iz, const int *rec_ix, int max_iter, int flags, float *times,
+                float *fields, int *iters, void *stream);
 
 /* Text of the last error on this context (never NULL). */
 const char *rtm_last_error(rtm_ctx *ctx);

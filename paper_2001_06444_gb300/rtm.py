@@ -18,6 +18,7 @@ from . import build as _build
 
 RTM_OK, RTM_ERR_ARG, RTM_ERR_CFL, RTM_ERR_NOMEM = 0, 1, 2, 3
 RTM_ERR_BUSY, RTM_ERR_TIMEOUT, RTM_ERR_CUDA, RTM_ERR_STATE = 4, 5, 6, 7
+EIK_OFFCHIP = 1
 SNAP_F32, SNAP_BF16, SNAP_F16 = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
@@ -28,7 +29,7 @@ EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_se
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
            "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
            "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
-           "rtm_compress", "rtm_decompress", "rtm_last_error", "rtm_cfl_limit")
+           "rtm_compress", "rtm_decompress", "rtm_eikonal", "rtm_last_error", "rtm_cfl_limit")
 
 
 class RTMError(RuntimeError):
@@ -61,7 +62,8 @@ class Stats(C.Structure):
                 ("step_bytes", C.c_double), ("point_updates", C.c_double),
                 ("launches", C.c_longlong), ("migrations", C.c_longlong),
                 ("codec_launches", C.c_longlong), ("codec_ms", C.c_double),
-                ("codec_bytes", C.c_double)]
+                ("codec_bytes", C.c_double), ("eik_launches", C.c_longlong),
+                ("eik_ms", C.c_double), ("eik_updates", C.c_double)]
 
 
 class Request(C.Structure):
@@ -108,6 +110,8 @@ def lib():
             L.rtm_compress.argtypes = [vp, vp, ll, ll, ll, C.c_double, vp, u64,
                                        C.POINTER(u64), vp]
             L.rtm_decompress.argtypes = [vp, vp, u64, ll, ll, ll, vp, vp]
+            L.rtm_eikonal.argtypes = [vp, ip, ip, C.c_double, C.c_double, ip, vp, ip, vp, vp, ip,
+                                      vp, vp, ip, ip, vp, vp, vp, vp]
             L.rtm_plan_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                          C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
             _lib = L
@@ -330,6 +334,31 @@ class Context:
                                          int(count), int(n0), int(n1),
                                          C.c_void_p(_ptr(out)[0]), _stream(streams, out)))
         return out
+
+    def eikonal(self, vel, dz: float, dx: float, src_iz, src_ix, rec_iz=None, rec_ix=None,
+                times=None, fields=None, max_iter: int = 0, offchip: bool = False):
+        """First-arrival traveltimes for vel [nsample][nz][nx] (or [nz][nx])
+        float32, host or device, from each source node; times [nsample][nsrc]
+        [nrec] at the receivers and/or fields [nsample][nsrc][nz][nx].
+        Returns the iterations each problem took (list)."""
+        _check_dtype(vel, "float32")
+        shape = tuple(int(v) for v in vel.shape)
+        ns, nz, nx = (1, *shape) if len(shape) == 2 else shape
+        siz = np.ascontiguousarray(np.atleast_1d(src_iz), np.int32)
+        six = np.ascontiguousarray(np.atleast_1d(src_ix), np.int32)
+        nrec = 0 if rec_iz is None else len(rec_iz)
+        riz = np.ascontiguousarray(rec_iz if nrec else np.zeros(1), np.int32)
+        rix = np.ascontiguousarray(rec_ix if nrec else np.zeros(1), np.int32)
+        it = (C.c_int * (ns * siz.size))()
+        tp = C.c_void_p(_ptr(times)[0]) if times is not None else None
+        fp = C.c_void_p(_ptr(fields)[0]) if fields is not None else None
+        arrays = [a for a in (vel, times, fields) if a is not None]
+        self._check(lib().rtm_eikonal(self.h, nz, nx, float(dz), float(dx), ns,
+                                      C.c_void_p(_ptr(vel)[0]), siz.size, siz.ctypes.data,
+                                      six.ctypes.data, nrec, riz.ctypes.data, rix.ctypes.data,
+                                      int(max_iter), EIK_OFFCHIP if offchip else 0, tp, fp, it,
+                                      _stream(*arrays)))
+        return list(it)
 
     def uncertainty_maps(self, mean, std, conf, ratio):
         npix = int(np.prod(mean.shape))
