@@ -334,16 +334,18 @@ int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long c
  * (RTM_ERR_ARG otherwise).  Sources and receivers: host arrays of node
  * indices.  times: [nsample][nsrc][nrec] s at the receivers, fields:
  * [nsample][nsrc][nz][nx] s, either may be NULL but not both; host or device.
- * flags: 0, or RTM_EIK_OFFCHIP to keep every problem's work field in an
- * L2-resident device buffer even when it fits in shared memory (more
- * problems per SM, each level of a sweep waiting on L2 instead of shared
- * memory); fields larger than shared memory are always kept that way.
+ * flags: where each problem's work field lives.  0 chooses: in shared
+ * memory (one problem per SM, the lowest latency per solve) when the
+ * problems fit one per SM, else in an L2-resident device buffer (many
+ * problems per SM, the highest throughput); RTM_EIK_OFFCHIP or RTM_EIK_SHARED
+ * force one (fields larger than shared memory always stay off chip).
  * max_iter (<= 0: 64) caps the iterations of four sweeps; iters (host,
  * nullable, [nsample * nsrc]) receives the iterations each problem took to
  * reach its fixed point (the last one changing nothing), -1 at the cap, in
  * which case the call returns RTM_ERR_STATE after writing every output.
  * Synchronises the stream. */
 #define RTM_EIK_OFFCHIP 1
+#define RTM_EIK_SHARED 2
 int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, int nsample,
                 const float *vel, int nsrc, const int *src_iz, const int *src_ix, int nrec,
                 const int *rec_iz, const int *rec_ix, int max_iter, int flags, float *times,

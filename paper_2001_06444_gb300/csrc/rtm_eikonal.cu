@@ -23,6 +23,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "rtm_engine.h"
@@ -30,12 +33,13 @@
 
 namespace {
 
+using u32 = uint32_t;
 constexpr float kInf = __builtin_huge_valf();
 
 struct EikArgs {
   const float *slow;     // [nsample][nz][nx] slowness (s/m)
   int nz, nx, nsrc, nrec;
-  float dz, dx, wz, wx, wsum, wprod;  // spacings, 1/dz^2, 1/dx^2, their sum and product
+  float dz, dx, wz, wx, wsum, wprod, inv_wsum;  // spacings, 1/dz^2, 1/dx^2, sum, product, 1/sum
   const int *src;        // [nsrc][2] (iz, ix)
   const int *rec;        // [nrec][2]
   float *times;          // [nsample][nsrc][nrec] or null
@@ -46,21 +50,94 @@ struct EikArgs {
 
 // The upwind update from the smaller vertical (a) and horizontal (b)
 // neighbour times: one-sided from the smaller one if that does not exceed
-// the other, else the larger root of the two-term quadratic.
+// the other, else the larger root of the two-term quadratic.  The root takes
+// the hardware reciprocal square root and a multiply by 1/(wz + wx): a few
+// ulps per update, far inside the FP32 error of a path of updates.
 __device__ __forceinline__ float update(float a, float b, float s, const EikArgs &A) {
   const bool vz = a <= b;
   const float u1 = vz ? a : b, u2 = vz ? b : a;
   const float h1 = vz ? A.dz : A.dx, w1 = vz ? A.wz : A.wx, w2 = vz ? A.wx : A.wz;
-  const float t1 = __fadd_rn(u1, __fmul_rn(s, h1));
+  const float t1 = u1 + s * h1;
   if (t1 <= u2) return t1;  // also both neighbours unknown: inf
-  const float d = __fsub_rn(u1, u2);
-  const float disc = __fsub_rn(__fmul_rn(A.wsum, __fmul_rn(s, s)), __fmul_rn(A.wprod, __fmul_rn(d, d)));
-  const float num = __fadd_rn(__fadd_rn(__fmul_rn(w1, u1), __fmul_rn(w2, u2)), __fsqrt_rn(fmaxf(disc, 0.f)));
-  return __fdiv_rn(num, A.wsum);
+  const float d = u1 - u2;
+  const float disc = fmaxf(A.wsum * (s * s) - A.wprod * (d * d), 1e-30f);
+  return (w1 * u1 + w2 * u2 + disc * rsqrtf(disc)) * A.inv_wsum;
 }
 
-template <bool RESIDENT>
-__global__ void __launch_bounds__(1024) k_eik_sweep(const __grid_constant__ EikArgs A) {
+// One tile of TZ x TX nodes, updated in the sweep's order by one thread: the
+// tile and its halo are loaded into registers, the nodes are updated one
+// after the other, and the changed values are stored.  Tiles on one tile
+// diagonal run in parallel; every node sees each neighbour in the same state
+// (updated in this sweep, or from the previous one) as in the sequential
+// sweep, so the result is the sequential sweep's, bit for bit.
+template <int TZ, int TX, bool FZ, bool FX>
+__device__ __forceinline__ bool sweep_tile(float *T, const float *s, int i0, int j0, int nz, int nx,
+                                           const EikArgs &A) {
+  float t[TZ][TX], sl[TZ][TX], up[TX], dn[TX], lf[TZ], rt[TZ];
+#pragma unroll
+  for (int r = 0; r < TZ; ++r) {
+    const int i = i0 + r;
+#pragma unroll
+    for (int c = 0; c < TX; ++c) {
+      const int j = j0 + c;
+      const bool in = i < nz && j < nx;
+      const long long k = (long long)i * nx + j;
+      t[r][c] = in ? T[k] : kInf;
+      sl[r][c] = in ? __ldg(s + k) : 0.f;
+    }
+    lf[r] = i < nz && j0 > 0 ? T[(long long)i * nx + j0 - 1] : kInf;
+    rt[r] = i < nz && j0 + TX < nx ? T[(long long)i * nx + j0 + TX] : kInf;
+  }
+#pragma unroll
+  for (int c = 0; c < TX; ++c) {
+    const int j = j0 + c;
+    up[c] = j < nx && i0 > 0 ? T[(long long)(i0 - 1) * nx + j] : kInf;
+    dn[c] = j < nx && i0 + TZ < nz ? T[(long long)(i0 + TZ) * nx + j] : kInf;
+  }
+  u32 changed = 0;
+#pragma unroll
+  for (int rr = 0; rr < TZ; ++rr) {
+    const int r = FZ ? rr : TZ - 1 - rr;
+#pragma unroll
+    for (int cc = 0; cc < TX; ++cc) {
+      const int c = FX ? cc : TX - 1 - cc;
+      if (i0 + r >= nz || j0 + c >= nx) continue;  // outside the grid: stays infinite
+      const float a = fminf(r > 0 ? t[r - 1][c] : up[c], r < TZ - 1 ? t[r + 1][c] : dn[c]);
+      const float b = fminf(c > 0 ? t[r][c - 1] : lf[r], c < TX - 1 ? t[r][c + 1] : rt[r]);
+      const float v = update(a, b, sl[r][c], A);
+      if (v < t[r][c]) {
+        t[r][c] = v;
+        changed |= 1u << (r * TX + c);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < TZ; ++r)
+#pragma unroll
+    for (int c = 0; c < TX; ++c)
+      if ((changed >> (r * TX + c)) & 1u) T[(long long)(i0 + r) * nx + j0 + c] = t[r][c];
+  return changed != 0;
+}
+
+template <int TZ, int TX, bool FZ, bool FX>
+__device__ __forceinline__ int sweep(float *T, const float *s, const EikArgs &A) {
+  const int nz = A.nz, nx = A.nx;
+  const int ntz = (nz + TZ - 1) / TZ, ntx = (nx + TX - 1) / TX;
+  int changed = 0;
+  for (int l = 0; l < ntz + ntx - 1; ++l) {
+    const int lo = max(0, l - (ntx - 1)), hi = min(ntz - 1, l);
+    for (int ip = lo + (int)threadIdx.x; ip <= hi; ip += blockDim.x) {
+      const int jp = l - ip;
+      const int ti = FZ ? ip : ntz - 1 - ip, tj = FX ? jp : ntx - 1 - jp;
+      changed |= sweep_tile<TZ, TX, FZ, FX>(T, s, ti * TZ, tj * TX, nz, nx, A);
+    }
+    __syncthreads();
+  }
+  return changed;
+}
+
+template <int TZ, int TX, bool RESIDENT>
+__global__ void __launch_bounds__(256, 4) k_eik_sweep(const __grid_constant__ EikArgs A) {
   extern __shared__ float s_T[];
   const int p = blockIdx.x;  // sample * nsrc + source
   const int sample = p / A.nsrc, src = p % A.nsrc;
@@ -75,27 +152,11 @@ __global__ void __launch_bounds__(1024) k_eik_sweep(const __grid_constant__ EikA
   int it = 0;
   bool converged = false;
   for (; it < A.max_iter; ++it) {
-    int changed = 0;
-#pragma unroll 1
-    for (int d = 0; d < 4; ++d) {
-      const bool fz = d == 0 || d == 3, fx = d < 2;  // (+,+), (+,-), (-,-), (-,+) in (z, x)
-      for (int l = 0; l < nz + nx - 1; ++l) {
-        const int lo = max(0, l - (nx - 1)), hi = min(nz - 1, l);
-        for (int ip = lo + (int)threadIdx.x; ip <= hi; ip += blockDim.x) {
-          const int jp = l - ip;
-          const int i = fz ? ip : nz - 1 - ip, j = fx ? jp : nx - 1 - jp;
-          const long long k = (long long)i * nx + j;
-          const float a = fminf(i > 0 ? T[k - nx] : kInf, i < nz - 1 ? T[k + nx] : kInf);
-          const float b = fminf(j > 0 ? T[k - 1] : kInf, j < nx - 1 ? T[k + 1] : kInf);
-          const float t = update(a, b, __ldg(s + k), A);
-          if (t < T[k]) {
-            T[k] = t;
-            changed = 1;
-          }
-        }
-        __syncthreads();
-      }
-    }
+    // the four diagonal directions: (+z, +x), (+z, -x), (-z, -x), (-z, +x)
+    int changed = sweep<TZ, TX, true, true>(T, s, A);
+    changed |= sweep<TZ, TX, true, false>(T, s, A);
+    changed |= sweep<TZ, TX, false, false>(T, s, A);
+    changed |= sweep<TZ, TX, false, true>(T, s, A);
     if (!__syncthreads_or(changed)) {
       converged = true;
       break;
@@ -147,26 +208,46 @@ cudaError_t launch_eikonal(const float *slow, int nsample, int nz, int nx, doubl
   A.wx = (float)(1.0 / (dx * dx));
   A.wsum = (float)(1.0 / (dz * dz) + 1.0 / (dx * dx));
   A.wprod = (float)(1.0 / (dz * dz * dx * dx));
+  A.inv_wsum = (float)(1.0 / (1.0 / (dz * dz) + 1.0 / (dx * dx)));
   A.src = src;
   A.rec = rec;
   A.times = times;
   A.fields = fields;
   A.max_iter = max_iter;
   A.iters = iters;
-  const int level = std::min(nz, nx);
-  const int threads = std::min(1024, std::max(32, (level + 31) / 32 * 32));
   const long long problems = (long long)nsample * nsrc;
   if (problems > 0x7fffffffll) return cudaErrorInvalidValue;
-  if (resident) {
-    const size_t smem = (size_t)nz * nx * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_eik_sweep<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_eik_sweep<true><<<(unsigned)problems, threads, smem, st>>>(A);
-  } else {
-    k_eik_sweep<false><<<(unsigned)problems, threads, 0, st>>>(A);
+  // tile shape: 2 x 2 (a short chain of dependent updates per thread, half
+  // the diagonals of single nodes); RTM_EIK_TILE=TZxTX overrides it (one of
+  // 1x1 2x2 2x4 4x2), for measurements
+  const int shapes[4][2] = {{2, 2}, {1, 1}, {2, 4}, {4, 2}};
+  int best = 0;
+  if (const char *env = getenv("RTM_EIK_TILE")) {
+    for (int q = 0; q < 4; ++q) {
+      char name[8];
+      snprintf(name, sizeof name, "%dx%d", shapes[q][0], shapes[q][1]);
+      if (!strcmp(env, name)) best = q;
+    }
   }
-  return cudaGetLastError();
+  const int tz = shapes[best][0], tx = shapes[best][1];
+  const int level = std::min((nz + tz - 1) / tz, (nx + tx - 1) / tx);  // tiles per diagonal
+  const int threads = std::min(256, std::max(32, (level + 31) / 32 * 32));
+  const size_t smem = resident ? (size_t)nz * nx * 4 : 0;
+  auto go = [&](auto kernel) -> cudaError_t {
+    if (resident) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kernel<<<(unsigned)problems, threads, smem, st>>>(A);
+    return cudaGetLastError();
+  };
+  switch (best) {
+    case 1: return resident ? go(k_eik_sweep<1, 1, true>) : go(k_eik_sweep<1, 1, false>);
+    case 2: return resident ? go(k_eik_sweep<2, 4, true>) : go(k_eik_sweep<2, 4, false>);
+    case 3: return resident ? go(k_eik_sweep<4, 2, true>) : go(k_eik_sweep<4, 2, false>);
+    default: return resident ? go(k_eik_sweep<2, 2, true>) : go(k_eik_sweep<2, 2, false>);
+  }
 }
 
 cudaError_t launch_eik_slowness(const float *vel, long long n, float *slow, cudaStream_t st) {
@@ -208,7 +289,8 @@ extern "C" int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, i
       return fail(ctx, RTM_ERR_ARG, "receiver %d at (%d, %d) is outside the grid", r, rec_iz[r],
                   rec_ix[r]);
   if (max_iter <= 0) max_iter = 64;
-  if (flags & ~RTM_EIK_OFFCHIP) return fail(ctx, RTM_ERR_ARG, "unknown flags %d", flags);
+  if ((flags & ~(RTM_EIK_OFFCHIP | RTM_EIK_SHARED)) || flags == (RTM_EIK_OFFCHIP | RTM_EIK_SHARED))
+    return fail(ctx, RTM_ERR_ARG, "bad flags %d", flags);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const long long N = (long long)nz * nx, problems = (long long)nsample * nsrc;
@@ -245,7 +327,11 @@ extern "C" int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, i
   }
   EIK_CU(dtab.alloc(ctx, tab.size() * 4, st));
   EIK_CU(cudaMemcpyAsync(dtab.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
-  const bool resident = !(flags & RTM_EIK_OFFCHIP) && (size_t)N * 4 <= eik_resident_limit();
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const bool fits = (size_t)N * 4 <= eik_resident_limit();
+  const bool resident = fits && !(flags & RTM_EIK_OFFCHIP) &&
+                        ((flags & RTM_EIK_SHARED) || problems <= (long long)sms);
   const size_t tbytes = (size_t)problems * nrec * 4, fbytes = (size_t)problems * N * 4;
   float *dt = times;
   if (times && !is_device_ptr(times)) {

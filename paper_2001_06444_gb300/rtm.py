@@ -18,7 +18,7 @@ from . import build as _build
 
 RTM_OK, RTM_ERR_ARG, RTM_ERR_CFL, RTM_ERR_NOMEM = 0, 1, 2, 3
 RTM_ERR_BUSY, RTM_ERR_TIMEOUT, RTM_ERR_CUDA, RTM_ERR_STATE = 4, 5, 6, 7
-EIK_OFFCHIP = 1
+EIK_OFFCHIP, EIK_SHARED = 1, 2
 SNAP_F32, SNAP_BF16, SNAP_F16 = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
@@ -336,11 +336,13 @@ class Context:
         return out
 
     def eikonal(self, vel, dz: float, dx: float, src_iz, src_ix, rec_iz=None, rec_ix=None,
-                times=None, fields=None, max_iter: int = 0, offchip: bool = False):
+                times=None, fields=None, max_iter: int = 0, storage: str = "auto"):
         """First-arrival traveltimes for vel [nsample][nz][nx] (or [nz][nx])
         float32, host or device, from each source node; times [nsample][nsrc]
         [nrec] at the receivers and/or fields [nsample][nsrc][nz][nx].
+        storage: "auto", "shared" or "offchip" (where the work fields live).
         Returns the iterations each problem took (list)."""
+        flags = {"auto": 0, "offchip": EIK_OFFCHIP, "shared": EIK_SHARED}[storage]
         _check_dtype(vel, "float32")
         shape = tuple(int(v) for v in vel.shape)
         ns, nz, nx = (1, *shape) if len(shape) == 2 else shape
@@ -356,7 +358,7 @@ class Context:
         self._check(lib().rtm_eikonal(self.h, nz, nx, float(dz), float(dx), ns,
                                       C.c_void_p(_ptr(vel)[0]), siz.size, siz.ctypes.data,
                                       six.ctypes.data, nrec, riz.ctypes.data, rix.ctypes.data,
-                                      int(max_iter), EIK_OFFCHIP if offchip else 0, tp, fp, it,
+                                      int(max_iter), flags, tp, fp, it,
                                       _stream(*arrays)))
         return list(it)
 

@@ -35,7 +35,8 @@ def _check(T, want):
     return err
 
 
-@pytest.mark.parametrize("shape", [(37, 53, 10.0, 15.0), (64, 31, 12.5, 12.5), (1, 40, 10.0, 10.0),
+@pytest.mark.parametrize("shape", [(37, 53, 10.0, 15.0), (64, 31, 12.5, 12.5), (100, 20, 10.0, 12.0),
+                                   (1, 40, 10.0, 10.0),
                                    (2, 2, 5.0, 7.0)])
 def test_fields_match_fast_marching(ctx, shape):
     nz, nx, dz, dx = shape
@@ -43,10 +44,10 @@ def test_fields_match_fast_marching(ctx, shape):
     src_iz = np.array([0, nz - 1, nz // 2], np.int32)
     src_ix = np.array([0, nx - 1, nx // 3], np.int32)
     outs = []
-    for offchip in (False, True):
+    for storage in ("shared", "offchip"):
         fields = torch.zeros((2, 3, nz, nx), dtype=torch.float32, device="cuda")
         iters = ctx.eikonal(torch.from_numpy(vel).cuda(), dz, dx, src_iz, src_ix, fields=fields,
-                            offchip=offchip)
+                            storage=storage)
         got = fields.cpu().numpy()
         for s in range(2):
             for k in range(3):
