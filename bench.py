@@ -433,12 +433,15 @@ def run_serve(args, local):
     print(json.dumps(serve_measurement(local, args.requests, args.rate)), flush=True)
 
 
-def run_ensemble(args, local):
+def run_ensemble(args, world, rank, local):
     """All (sample, shot) migrations of a velocity ensemble in one call, then
-    the per-pixel statistics of the images."""
+    the per-pixel statistics of the images.  Under torchrun each rank
+    migrates a contiguous share of the samples; the statistics then take the
+    pixel-slab exchange (over gloo, through host copies)."""
     import torch
 
     from paper_2001_06444_gb300 import inputs, rtm
+    from paper_2001_06444_gb300.sharding import share, sharded_ensemble_stats
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -453,34 +456,46 @@ def run_ensemble(args, local):
     vt = torch.from_numpy(s.vel.astype(np.float32)).to(dev)
     seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
     ctx.model(grid, vt, acq, -1, seis)
-    vels = torch.from_numpy(ens.astype(np.float32)).to(dev)
-    imgs = torch.empty((args.samples, s.nz, s.nx), dtype=torch.float32, device=dev)
+    a, b = share(args.samples, rank, world)
+    vels = torch.from_numpy(ens[a:b].astype(np.float32)).to(dev)
+    imgs = torch.empty((b - a, s.nz, s.nx), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
     ctx.set_profiling(True)
     ctx.stats(reset=True)
+    barrier(world)
     t = time.perf_counter()
     ctx.migrate_ensemble(grid, vels, acq, seis, rtm.Opts(4, snap, 1e-6, 1), imgs)
     torch.cuda.synchronize()
-    mig_s = time.perf_counter() - t
+    mig_s = max_over_ranks(time.perf_counter() - t, world)
     st = ctx.stats(reset=True)
     npix = s.nz * s.nx
-    outs = [torch.empty(npix, dtype=tp, device=dev)
-            for tp in (torch.float64, torch.float64, torch.float32, torch.float32)]
+
+    def gpu_stats(slab):
+        d = slab.to(dev).contiguous()
+        outs = [torch.empty(d.shape[1], dtype=tp, device=dev)
+                for tp in (torch.float64, torch.float64, torch.float32, torch.float32)]
+        ctx.ensemble_stats(d, *outs)
+        return [o.cpu() if world > 1 else o for o in outs]
+
+    barrier(world)
     t = time.perf_counter()
-    ctx.ensemble_stats(imgs, *outs)
+    local = imgs.reshape(b - a, npix)
+    sharded_ensemble_stats(local.cpu() if world > 1 else local, args.samples, rank, world,
+                           gpu_stats)
     torch.cuda.synchronize()
-    stats_s = time.perf_counter() - t
+    stats_s = max_over_ranks(time.perf_counter() - t, world)
     peak, _ = measured_peaks()
     achieved = st["step_bytes"] / (st["step_ms"] / 1e3) / 1e9
-    line = {
-        "workload": f"ensemble_{args.samples}x{s.nshot}_1701x351_nt{s.nt}_{args.snap}snap",
-        "migrations": args.samples * s.nshot, "migration_s": mig_s,
-        "shots_per_s": args.samples * s.nshot / mig_s,
-        "gpt_updates_per_s": st["point_updates"] / mig_s / 1e9,
-        "step_kernel_gbs": achieved, "frac_of_measured_hbm": achieved / peak,
-        "stats_ms": 1e3 * stats_s,
-    }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        line = {
+            "workload": f"ensemble_{args.samples}x{s.nshot}_1701x351_nt{s.nt}_{args.snap}snap",
+            "n_gpus": world, "migrations": args.samples * s.nshot, "migration_s": mig_s,
+            "shots_per_s": args.samples * s.nshot / mig_s,
+            "gpt_updates_per_s": st["point_updates"] * world / mig_s / 1e9,
+            "step_kernel_gbs": achieved, "frac_of_measured_hbm": achieved / peak,
+            "stats_ms": 1e3 * stats_s,
+        }
+        print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -675,7 +690,7 @@ def main():
     elif args.workload == "serve":
         run_serve(args, local)
     elif args.workload == "ensemble":
-        run_ensemble(args, local)
+        run_ensemble(args, world, rank, local)
     elif args.workload == "codec":
         run_codec(args, local)
     elif args.workload == "eikonal":
