@@ -273,10 +273,18 @@ def run_native(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
         v, dt, cores = cpu_baseline(s, vm, nshot=2)
         cpu = {"value": v, "unit": "shots/s", "cores": cores, "kind": "oracle",
                "sample": f"2 of the {s.nshot} shots, all {s.nt} steps (fwd+bwd+imaging, FP64), "
                          f"{dt:.1f} s"}
+        oracle.set_threads(1)
+        v1, dt1, _ = cpu_baseline(s, vm, nshot=1, nt=300)
+        oracle.set_threads(cores)
+        cpu["single_thread_value"] = v1
+        cpu["single_thread_sample"] = (f"1 shot, 300 of {s.nt} steps on 1 thread, {dt1:.1f} s, "
+                                       f"extrapolated linearly in steps")
 
     ctx.close()
     serving = None

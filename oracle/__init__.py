@@ -89,6 +89,8 @@ def lib():
             L.oracle_codec_compress.restype = C.c_uint64
             L.oracle_codec_decompress.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
                                                   C.c_int64]
+            L.oracle_set_threads.argtypes = [C.c_int]
+            L.oracle_set_threads.restype = None
             L.oracle_eikonal_update.argtypes = [C.c_double] * 5
             L.oracle_eikonal_update.restype = C.c_double
             L.oracle_eikonal.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_void_p,
@@ -223,6 +225,11 @@ def sponge(g: Grid):
 def threads() -> int:
     """Threads the oracle's OpenMP loops use."""
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Set the threads of the oracle's OpenMP loops."""
+    lib().oracle_set_threads(int(n))
 
 
 # ---------------------------------------------------------------- codec --

@@ -402,6 +402,16 @@ int oracle_threads(void) {
 #endif
 }
 
+/* Set the threads of the oracle's parallel loops (n >= 1). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* The padded-grid sponge factor g, exposed for tests: [NZ][NX]. */
 int oracle_sponge(const or_grid *gr, double *g) {
   int NZ = gr->nz + 2 * gr->nb, NX = gr->nx + 2 * gr->nb;
