@@ -337,3 +337,37 @@ def test_two_step_kernel_matches_single_step_bitwise(ctx):
             assert np.array_equal(a, b), (isnap, mode)
     finally:
         one.close()
+
+
+def test_full_size_ensemble_sampled_parity(ctx):
+    """The 64-sample ensemble at full size (1701 x 351, 5000 steps, GRF
+    perturbations of the 60 m-smoothed model) through one migrate_ensemble
+    call, one shot: samples 0 and 63 against the oracle's migration, and the
+    per-pixel statistics of all 64 images against the oracle's statistics of
+    the same images."""
+    s = inputs.full_size(nshot=96)
+    shot = 30
+    one = inputs.Survey(s.nx, s.nz, s.nb, s.dx, s.dz, s.dt, s.nt, s.vel, s.src_ix[shot:shot + 1],
+                        s.src_iz[shot:shot + 1], s.rec_ix, s.rec_iz, s.wavelet)
+    data = f32(ora_model(one, s.vel))[None]
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    ens = f32(inputs.ensemble(vm, s.dx, s.dz, 64))
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, one.src_ix, one.src_iz, one.rec_ix, one.rec_iz, f32(one.wavelet))
+    imgs = torch.zeros((64, s.nz, s.nx), dtype=torch.float32, device="cuda")
+    ctx.migrate_ensemble(rtm.make_grid(*one.grid_tuple()), dev(ens), acq, dev(data),
+                         rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1), imgs)
+    npix = s.nz * s.nx
+    out = [torch.zeros(npix, dtype=t, device="cuda")
+           for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    ctx.ensemble_stats(imgs, *out)
+    torch.cuda.synchronize()
+    got = imgs.cpu().numpy()
+    for k in (0, 63):
+        assert rel_l2(got[k], ora_migrate(one, ens[k], data, isnap=4)) <= IMG_TOL, k
+    mean, std, q05, q95 = [o.cpu().numpy() for o in out]
+    m, sd, a, b = oracle.ensemble_stats(got.reshape(64, npix))
+    assert np.allclose(mean, m, rtol=1e-12, atol=1e-13 * np.abs(m).max())
+    assert np.allclose(std, sd, rtol=1e-12, atol=1e-13 * np.abs(sd).max())
+    assert np.array_equal(q05, a.astype(np.float32))
+    assert np.array_equal(q95, b.astype(np.float32))
