@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--nt", type=int, default=5000)
     # other workloads of the method, each printing its own JSON line
     p.add_argument("--workload", default="migrate",
-                   choices=["migrate", "ensemble", "serve", "codec", "eikonal"])
+                   choices=["migrate", "ensemble", "serve", "codec", "eikonal", "stats"])
     p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
@@ -692,6 +692,41 @@ def run_eikonal(args, local):
     ctx.close()
 
 
+def run_stats(args, local):
+    """Per-pixel ensemble statistics (mean, std, 5/95 % quantiles) of
+    --samples seeded normal images of the 351 x 1701 grid, device buffers;
+    CUDA events around --steps calls after --warmup calls."""
+    import torch
+
+    from paper_2001_06444_gb300 import rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, npix = args.samples, 351 * 1701
+    g = torch.Generator(device=dev).manual_seed(2001064)
+    x = torch.randn((n, npix), generator=g, device=dev, dtype=torch.float32)
+    outs = [torch.empty(npix, dtype=t, device=dev)
+            for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    ctx = rtm.Context(local)
+    for _ in range(args.warmup):
+        ctx.ensemble_stats(x, *outs)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.ensemble_stats(x, *outs)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    nbytes = n * npix * 4 + npix * 24
+    peak, kind = measured_peaks()
+    print(json.dumps({"workload": f"ensemble_stats_{n}x{npix}", "ms_per_call": ms,
+                      "algorithmic_gbs": nbytes / ms / 1e6, "frac_of_hbm": nbytes / ms / 1e6 / peak,
+                      "peak_kind": kind, "data": "synthetic"}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -705,6 +740,8 @@ def main():
         run_codec(args, local)
     elif args.workload == "eikonal":
         run_eikonal(args, local)
+    elif args.workload == "stats":
+        run_stats(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:
