@@ -30,14 +30,16 @@ def _model(seed, nz, nx, dz, dx):
 
 def _check(T, want):
     assert np.all(np.isfinite(T))
+    if want.max() == 0.0:  # a grid that is only its source
+        assert np.all(T == 0.0)
+        return 0.0
     err = np.abs(T.astype(np.float64) - want).max() / want.max()
     assert err <= TOL, err
     return err
 
 
 @pytest.mark.parametrize("shape", [(37, 53, 10.0, 15.0), (64, 31, 12.5, 12.5), (100, 20, 10.0, 12.0),
-                                   (1, 40, 10.0, 10.0),
-                                   (2, 2, 5.0, 7.0)])
+                                   (1, 40, 10.0, 10.0), (2, 2, 5.0, 7.0), (1, 1, 10.0, 10.0)])
 def test_fields_match_fast_marching(ctx, shape):
     nz, nx, dz, dx = shape
     vel = np.stack([_model(s, nz, nx, dz, dx) for s in (1, 2)])

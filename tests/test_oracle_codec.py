@@ -183,3 +183,12 @@ def test_malformed_streams_are_rejected():
         oracle.codec_decompress(bytes(bad), 30, 30)  # magic
     with pytest.raises(ValueError):
         oracle.codec_compress(np.full((4, 4), np.nan, np.float32), 1e-3)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (130, 1), (5, 3)])
+def test_degenerate_shapes(shape):
+    x = inputs.normal(13, shape[0] * shape[1]).reshape(shape).astype(np.float32)
+    y = oracle.codec_decompress(oracle.codec_compress(x, 1e-3), *shape)
+    assert np.all(np.abs(y.astype(np.float64) - x) <= 1e-3)
+    y = oracle.codec_decompress(oracle.codec_compress(x, 0.0), *shape)
+    assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
