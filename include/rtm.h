@@ -215,6 +215,20 @@ int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample,
                          const float *seis, const rtm_opts *opts,
                          float *images, void *stream);
 
+/* Born (linearised) modelling, the adjoint of the imaging numerator of Eq. 5
+ * and the forward operator of least-squares migration: the source
+ * wavefield of each shot of acq is propagated in vel and kept at the imaging
+ * steps k (k mod isnap == 0) in opts->snap_dtype, and a perturbation field,
+ * at rest at first, is driven at those steps by the secondary source
+ * c m S^k (c = (v dt)^2, m = refl [nz][nx] at each physical pixel) and
+ * recorded like rtm_model: seis [nshot][nt][nrec], d[n][r] = du^{n+1}(r).
+ * <born(m), d> equals <m, num(d)> where num is the migration's
+ * unnormalised numerator.  opts->eps and opts->laplacian are not used;
+ * opts->checkpoint must be 0 (RTM_ERR_ARG).  Arrays host or device; checks
+ * the CFL bound like rtm_migrate. */
+int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,
+             const float *refl, const rtm_opts *opts, float *seis, void *stream);
+
 /* Per-pixel statistics of n images (§2.3; stage 3 of §3): mean and standard
  * deviation (divisor n-1; 0 when n == 1) reduced in FP64, and the 5% and 95%
  * quantiles (linear interpolation between order statistics at h = (n-1) p).

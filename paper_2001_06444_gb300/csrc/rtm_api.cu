@@ -563,7 +563,8 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
 
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
-                   int B, cudaStream_t st, const RunConfig &cfg) {
+                   int B, cudaStream_t st, const RunConfig &cfg, const float *born_refl,
+                   float *born_out) {
   Common C;
   int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel);
   if (rc) return rc;
@@ -728,6 +729,29 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
       rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, true, false); });
       if (rc) return rc;
       if ((rc = mark())) return rc;
+      if (born_refl) {
+        // Born modelling: the perturbation field starts at rest; each step
+        // adds c m S^{n+1} on imaging steps and records the receivers
+        if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
+        A.refl = born_refl;
+        A.rec_out = born_out + (size_t)q0 * nt * acq.nrec;
+        if ((rc = mark())) return rc;
+        rc = run_phase(ctx, graph, st, [&]() -> int {
+          for (int n = 0; n < nt; ++n) {
+            StepRT r{};
+            r.n = n;
+            r.snap_idx = r.max_idx = -1;
+            r.img_idx = inK(n + 1) ? (n + 1) / isnap - 1 : -1;
+            const int r2 = step1(ctx, MODE_BORN, A, F, r, nb, st);
+            if (r2) return r2;
+            ++step_launches;
+          }
+          return RTM_OK;
+        });
+        if (rc) return rc;
+        if ((rc = mark())) return rc;
+        continue;
+      }
       if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
       if ((rc = mark())) return rc;
       rc = run_phase(ctx, graph, st, [&]() { return bwd_range(F, nt, 0, 0); });
@@ -764,10 +788,13 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     launches += 1;
   }
   launches += step_launches;
-  CU(launch_filter(stack.as<float>(), comp.as<float>(), nsample, g.nz, g.nx, g.SX,
-                   (float)(1.0 / (gr.dz * gr.dz)), (float)(1.0 / (gr.dx * gr.dx)), op.laplacian,
-                   img_d, st));
-  launches += 2;  // prep_c, filter
+  if (!born_refl) {
+    CU(launch_filter(stack.as<float>(), comp.as<float>(), nsample, g.nz, g.nx, g.SX,
+                     (float)(1.0 / (gr.dz * gr.dz)), (float)(1.0 / (gr.dx * gr.dx)),
+                     op.laplacian, img_d, st));
+    launches += 1;
+  }
+  launches += 1;  // prep_c
   CU(cudaMemcpyAsync(ctx->h_err, C.err.p, 4, cudaMemcpyDeviceToHost, st));
   double ms_total = 0.0;
   if (ctx->prof) {
@@ -1235,6 +1262,52 @@ int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const 
                          const rtm_acq *acq, const float *seis, const rtm_opts *opts,
                          float *images, void *stream) {
   return migrate_common(ctx, grid, nsample, vels, acq, seis, opts, images, stream);
+}
+
+int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,
+             const float *refl, const rtm_opts *opts, float *seis, void *stream) {
+  if (!ctx) return RTM_ERR_ARG;
+  int rc;
+  if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true)) ||
+      (rc = check_opts(ctx, opts)))
+    return rc;
+  if (!vel || !refl || !seis) return fail(ctx, RTM_ERR_ARG, "NULL array argument");
+  if (opts->checkpoint)
+    return fail(ctx, RTM_ERR_ARG, "Born modelling keeps every snapshot (checkpoint must be 0)");
+  if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vbytes = (size_t)grid->nx * grid->nz * 4;
+  const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
+  const MigrationPlan plan = plan_migration(*grid, *acq, *opts, 1);
+  const size_t io = (is_device_ptr(vel) ? 0 : vbytes) + (is_device_ptr(refl) ? 0 : vbytes) +
+                    (is_device_ptr(seis) ? 0 : sbytes);
+  const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
+  const RunConfig cfg = config_for(ctx, *grid, *opts);
+  size_t want = plan.shared_bytes + io + (size_t)acq->nshot * plan.item_bytes;
+  const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
+  if (cap > 0) want = std::min(want, plan.shared_bytes + io + (size_t)cap * plan.item_bytes);
+  if (need1 > ctx->budget)
+    return fail(ctx, RTM_ERR_NOMEM, "one Born modelling needs %.3f GB, budget is %.3f GB",
+                need1 / 1e9, ctx->budget / 1e9);
+  const size_t got = reserve_wait(ctx, want, need1, 600000);
+  if (!got) return fail(ctx, RTM_ERR_TIMEOUT, "waited 600 s for %.3f GB of the budget", need1 / 1e9);
+  const long long nitems = acq->nshot;
+  long long bmax = std::max<long long>(
+      1, std::min<long long>(nitems, (long long)((got - plan.shared_bytes - io) / plan.item_bytes)));
+  const long long nbatch = (nitems + bmax - 1) / bmax;
+  const int B = (int)((nitems + nbatch - 1) / nbatch);
+  View v, m, out;
+  rc = view_in(ctx, v, vel, vbytes, st);
+  if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)grid->nx * grid->nz, st);
+  if (!rc) rc = view_in(ctx, m, refl, vbytes, st);
+  if (!rc) rc = view_out(ctx, out, seis, sbytes, st);
+  if (!rc)
+    rc = migrate_device(ctx, *grid, 1, v.d, *acq, nullptr, *opts, nullptr, B, st, cfg, m.d,
+                        out.d);
+  if (!rc) rc = view_finish(ctx, out, seis, sbytes, st);
+  if (!rc && (out.staged || ctx->prof)) rc = check_wait_flag(ctx);
+  unreserve(ctx, got);
+  return rc;
 }
 
 int rtm_ensemble_stats(rtm_ctx *ctx, const float *images, int n, long npix, double *mean,

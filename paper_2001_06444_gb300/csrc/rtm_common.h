@@ -62,6 +62,7 @@ struct StepArgs {
   unsigned *smax;            // [B][nsnap] max |S^k| as float bits
   float *num, *den;          // [B][pplane] imaging accumulators
   unsigned *dmax;            // [B] max of den as float bits
+  const float *refl;         // [nz][nx] reflectivity m of the Born operator
 };
 
 // Per-launch scalars.
@@ -70,7 +71,8 @@ struct StepRT {
                   // backward: k of the produced field w^k
   int snap_idx;   // forward: store the CURRENT field u^n as snapshot snap_idx (-1 none)
   int max_idx;    // forward: reduce max |u^{n+1}| into slot max_idx (-1 none)
-  int img_idx;    // backward: image with snapshot img_idx (-1 none)
+  int img_idx;    // backward: image with snapshot img_idx (-1 none); Born:
+                  // inject c m S from snapshot img_idx into the new field
   int dmax_flag;  // backward: after imaging, reduce max(den) into dmax
 };
 
@@ -115,6 +117,6 @@ struct Step2RT {
   int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
 };
 
-enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2 };
+enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2, MODE_BORN = 3 };
 
 }  // namespace rtm

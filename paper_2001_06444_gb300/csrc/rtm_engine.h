@@ -96,9 +96,13 @@ int check_opts(rtm_ctx *ctx, const rtm_opts *o);
 
 // Migration of nsample models x all shots with device pointers and a fixed
 // batch size B (items in flight).  Memory is allocated from the pool.
+// With born_refl set, Born modelling instead: the backward phase is replaced
+// by the perturbation field driven by c m S^k, recorded into born_out
+// [nitems][nt][nrec]; seis_d and img_d are not used.
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
-                   int B, cudaStream_t st, const RunConfig &cfg);
+                   int B, cudaStream_t st, const RunConfig &cfg,
+                   const float *born_refl = nullptr, float *born_out = nullptr);
 RunConfig config_for(rtm_ctx *ctx, const rtm_grid &gr, const rtm_opts &op);
 
 // Velocity range check (CFL of §3, positivity, finiteness); synchronises st.

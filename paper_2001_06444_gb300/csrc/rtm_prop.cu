@@ -199,12 +199,35 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
     }
   }
 
+  // 3b. Born modelling: the secondary source c m S^{n+1} of the perturbation
+  //     field at every physical pixel, on imaging steps
+  const int j0 = col - g.CP;  // physical column of lane 0 (multiple of 4)
+  const bool jok = j0 >= 0 && j0 < g.SX;
+  if (MODE == MODE_BORN && rt.img_idx >= 0 && jok) {
+    float sdq, inv;
+    snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_idx], sdq, inv);
+    const long long sbase = ((long long)b * A.nsnap + rt.img_idx) * g.pplane + j0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = row0 + r - g.nb;
+      if (i >= 0 && i < g.nz) {
+        const float4 S = snap_load4(A.snap, sbase + (long long)i * g.SX, A.snap_dtype, sdq);
+        const float Sv[4] = {S.x, S.y, S.z, S.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+          if (j0 + l < g.nx)
+            res[r][l] = fmaf(lane4(cv[r], l) * __ldg(A.refl + (long long)i * g.nx + j0 + l), Sv[l],
+                             res[r][l]);
+      }
+    }
+  }
+
   // 4. injection / recording through shared memory (only blocks that own
   //    a source or receiver cell; the condition is block-uniform)
   const int shot = A.item_shot[b];
   bool stage = false;
   int sr = -1, scl = -1, rp0 = 0, rp1 = 0;
-  if (MODE != MODE_BWD) {
+  if (MODE == MODE_FWD || MODE == MODE_MODEL) {
     sr = A.src_row[shot] - z0;
     scl = A.src_col[shot] - x0;
     if (sr >= 0 && sr < TZ && scl >= 0 && scl < TX)
@@ -225,12 +248,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
       *reinterpret_cast<float4 *>(&s[HALO + 4 * ty + r][sc]) =
           make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
     __syncthreads();
-    if (MODE != MODE_BWD) {
+    if (MODE == MODE_FWD || MODE == MODE_MODEL) {
       if (sr >= 0 && tid == 0) {
         const long long o = (long long)(z0 + sr) * g.P + (x0 + scl);
         s[HALO + sr][HALO + scl] += cc[o] * (A.wav[rt.n] * A.src_scale);
       }
-    } else {
+    } else if (MODE == MODE_BWD) {
       const float *d = A.seis + ((long long)shot * A.nt + (rt.n - 1)) * A.nrec;
       for (int e = rp0 + tid; e < rp1; e += STEP_THREADS) {
         const int2 en = A.rtile_ent[e];
@@ -240,7 +263,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
       }
     }
     __syncthreads();
-    if (MODE == MODE_MODEL) {
+    if (MODE == MODE_MODEL || MODE == MODE_BORN) {
       float *ro = A.rec_out + ((long long)b * A.nt + rt.n) * A.nrec;
       for (int e = rp0 + tid; e < rp1; e += STEP_THREADS) {
         const int2 en = A.rtile_ent[e];
@@ -273,9 +296,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
       *reinterpret_cast<float4 *>(out + o) = make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
     }
   }
-
-  const int j0 = col - g.CP;  // physical column of lane 0 (multiple of 4)
-  const bool jok = j0 >= 0 && j0 < g.SX;
 
   // 6. forward: store the current field as a snapshot, reduce the new max
   if (MODE == MODE_FWD) {
@@ -415,6 +435,8 @@ cudaError_t launch_step(int mode, const StepArgs &A, const StepRT &rt, int B, cu
     k_step<MODE_FWD><<<grid, block, 0, st>>>(A, rt);
   else if (mode == MODE_MODEL)
     k_step<MODE_MODEL><<<grid, block, 0, st>>>(A, rt);
+  else if (mode == MODE_BORN)
+    k_step<MODE_BORN><<<grid, block, 0, st>>>(A, rt);
   else
     k_step<MODE_BWD><<<grid, block, 0, st>>>(A, rt);
   return cudaGetLastError();

@@ -27,8 +27,8 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 # every entry point the header declares
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
-           "rtm_migrate_ensemble", "rtm_ensemble_stats", "rtm_uncertainty_maps", "rtm_submit",
-           "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
+           "rtm_migrate_ensemble", "rtm_born", "rtm_ensemble_stats", "rtm_uncertainty_maps",
+           "rtm_submit", "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
            "rtm_compress", "rtm_decompress", "rtm_eikonal", "rtm_last_error", "rtm_cfl_limit")
 
 
@@ -93,6 +93,8 @@ def lib():
                                       vp, vp]
             L.rtm_migrate_ensemble.argtypes = [vp, C.POINTER(Grid), ip, vp, C.POINTER(Acq), vp,
                                                C.POINTER(Opts), vp, vp]
+            L.rtm_born.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Acq), vp, C.POINTER(Opts), vp,
+                                   vp]
             L.rtm_ensemble_stats.argtypes = [vp, vp, ip, C.c_long, vp, vp, vp, vp, vp]
             L.rtm_uncertainty_maps.argtypes = [vp, vp, vp, C.c_long, vp, vp, vp]
             L.rtm_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
@@ -292,6 +294,16 @@ class Context:
                                                C.byref(acq), C.c_void_p(ps), C.byref(opts),
                                                C.c_void_p(pi), _stream(vels, seis, images)))
         return images
+
+    def born(self, grid: Grid, vel, acq: Acq, refl, opts: Opts, seis):
+        """Born modelling of every shot of acq: reflectivity refl [nz][nx] ->
+        seis [nshot][nt][nrec] (float32, host or device)."""
+        for a in (vel, refl, seis):
+            _check_dtype(a, "float32")
+        ptrs = [C.c_void_p(_ptr(a)[0]) for a in (vel, refl, seis)]
+        self._check(lib().rtm_born(self.h, C.byref(grid), ptrs[0], C.byref(acq), ptrs[1],
+                                   C.byref(opts), ptrs[2], _stream(vel, refl, seis)))
+        return seis
 
     def ensemble_stats(self, images, mean, std, q05, q95):
         _check_dtype(images, "float32")

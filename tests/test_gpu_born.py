@@ -1,0 +1,93 @@
+"""GPU Born modelling (rtm_born) against the FP64 oracle's Born operator,
+which the oracle's dot test pins as the exact adjoint of the migration
+numerator: several shots in one batch, snapshot intervals 1, 3 and 4, FP32
+and FP16 snapshots, host buffers; a batch split does not change the data."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_l2
+from paper_2001_06444_gb300 import inputs, rtm
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+SEIS_TOL, HALF_TOL = 1e-4, 1e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rtm.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def problem():
+    nx, nz, nt = 160, 80, 400
+    v = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=31, water_depth=100.0)
+    vm = inputs.smooth(v, 10.0, 10.0, 40.0).astype(np.float32)
+    refl = ((v - inputs.smooth(v, 10.0, 10.0, 40.0)) / v).astype(np.float32)  # a sharp contrast map
+    s = inputs.Survey(nx, nz, 16, 10.0, 10.0, 1e-3, nt, vm, np.array([10, 80, 151], np.int32),
+                      np.array([1, 2, 1], np.int32), np.arange(0, nx, 3, dtype=np.int32),
+                      np.full(len(range(0, nx, 3)), 1, np.int32), inputs.ricker(18.0, 1e-3, nt))
+    return s, vm, refl
+
+
+def _oracle(s, vm, refl, isnap):
+    g = oracle.grid(*s.grid_tuple())
+    w = s.wavelet.astype(np.float32).astype(np.float64)
+    return np.stack([oracle.born(g, vm.astype(np.float64), s.src_ix[k], s.src_iz[k], s.rec_ix,
+                                 s.rec_iz, w, isnap, refl.astype(np.float64))
+                     for k in range(len(s.src_ix))])
+
+
+def _gpu(ctx, s, vm, refl, isnap, dtype=rtm.SNAP_F32, host=False):
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    out = np.zeros((len(s.src_ix), s.nt, len(s.rec_ix)), np.float32)
+    if host:
+        ctx.born(rtm.make_grid(*s.grid_tuple()), vm, acq, refl, rtm.Opts(isnap, dtype, 1e-6, 0), out)
+        return out
+    d = torch.from_numpy(out).cuda()
+    ctx.born(rtm.make_grid(*s.grid_tuple()), torch.from_numpy(vm).cuda(), acq,
+             torch.from_numpy(refl).cuda(), rtm.Opts(isnap, dtype, 1e-6, 0), d)
+    torch.cuda.synchronize()
+    return d.cpu().numpy()
+
+
+@pytest.mark.parametrize("isnap", [1, 3, 4])
+def test_born_matches_oracle(ctx, problem, isnap):
+    s, vm, refl = problem
+    want = _oracle(s, vm, refl, isnap)
+    got = _gpu(ctx, s, vm, refl, isnap)
+    for k in range(len(s.src_ix)):
+        assert rel_l2(got[k], want[k]) <= SEIS_TOL, (isnap, k)
+
+
+def test_born_half_snapshots_and_host_buffers(ctx, problem):
+    s, vm, refl = problem
+    want = _oracle(s, vm, refl, 4)
+    got = _gpu(ctx, s, vm, refl, 4, dtype=rtm.SNAP_F16, host=True)
+    assert max(rel_l2(got[k], want[k]) for k in range(len(s.src_ix))) <= HALF_TOL
+
+
+def test_born_batch_split_is_invariant(ctx, problem):
+    s, vm, refl = problem
+    full = _gpu(ctx, s, vm, refl, 4)
+    ctx.set_batch(1)
+    try:
+        one = _gpu(ctx, s, vm, refl, 4)
+    finally:
+        ctx.set_batch(0)
+    assert np.array_equal(full, one)
+
+
+def test_born_refuses_checkpoint_mode(ctx, problem):
+    s, vm, refl = problem
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    out = np.zeros((len(s.src_ix), s.nt, len(s.rec_ix)), np.float32)
+    with pytest.raises(rtm.RTMError) as ei:
+        ctx.born(rtm.make_grid(*s.grid_tuple()), vm, acq, refl, rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0, 80),
+                 out)
+    assert ei.value.code == rtm.RTM_ERR_ARG
