@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--nt", type=int, default=5000)
     # other workloads of the method, each printing its own JSON line
     p.add_argument("--workload", default="migrate",
-                   choices=["migrate", "ensemble", "serve", "codec", "eikonal", "stats"])
+                   choices=["migrate", "ensemble", "serve", "codec", "eikonal", "stats", "born"])
     p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
@@ -727,6 +727,54 @@ def run_stats(args, local):
     ctx.close()
 
 
+def run_born(args, local):
+    """Born modelling of the full-size survey (the forward operator of
+    least-squares migration): --shots shots of the 1701 x 351 model,
+    reflectivity = the relative contrast of the true model against the 60 m
+    smoothed one, FP32 snapshots every 4 steps; CUDA events around --steps
+    calls after --warmup calls."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = inputs.full_size(nshot=args.shots, nt=args.nt)
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    refl = ((s.vel - vm) / s.vel).astype(np.float32)
+    grid = rtm.make_grid(*s.grid_tuple())
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    opts = rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0, 0)
+    ctx = rtm.Context(local)
+    vel = torch.from_numpy(vm.astype(np.float32)).to(dev)
+    m = torch.from_numpy(refl).to(dev)
+    seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.born(grid, vel, acq, m, opts, seis)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.stats(reset=True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.born(grid, vel, acq, m, opts, seis)
+    e1.record(st)
+    torch.cuda.synchronize()
+    stt = ctx.stats(reset=True)
+    ms = e0.elapsed_time(e1) / args.steps
+    peak, _ = measured_peaks()
+    print(json.dumps({
+        "workload": f"born_1701x351_{s.nshot}shots_nt{s.nt}_isnap4_f32snap",
+        "shots_per_s": s.nshot / (ms / 1e3), "ms_per_step": ms,
+        "gpt_updates_per_s": stt["point_updates"] / args.steps / (ms / 1e3) / 1e9,
+        "step_kernel_gbs": stt["step_bytes"] / (stt["step_ms"] / 1e3) / 1e9,
+        "frac_of_measured_hbm": stt["step_bytes"] / (stt["step_ms"] / 1e3) / 1e9 / peak,
+        "data": "synthetic"}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -742,6 +790,8 @@ def main():
         run_eikonal(args, local)
     elif args.workload == "stats":
         run_stats(args, local)
+    elif args.workload == "born":
+        run_born(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:
