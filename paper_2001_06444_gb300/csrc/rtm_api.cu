@@ -609,7 +609,10 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   // recomputation in checkpoint mode is overhead, not counted
   const double upd = (double)g.NZ * g.NX, pix = (double)g.nz * g.nx;
   const double fwd_bytes = gr.nt * 16.0 * upd + nsnap * (double)esz * pix;
-  const double bwd_bytes = gr.nt * 16.0 * upd + nsnap * ((double)esz + 16.0) * pix;
+  // (Born modelling's second phase reads a snapshot and the reflectivity per
+  // pixel on imaging steps instead of updating num and den)
+  const double bwd_bytes = gr.nt * 16.0 * upd +
+                           nsnap * ((double)esz + (born_refl ? 4.0 : 16.0)) * pix;
   long long launches = 0, step_launches = 0;
   std::vector<cudaEvent_t> ev;
   auto mark = [&]() -> int {
@@ -733,16 +736,31 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
         // Born modelling: the perturbation field starts at rest; each step
         // adds c m S^{n+1} on imaging steps and records the receivers
         if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
-        A.refl = born_refl;
-        A.rec_out = born_out + (size_t)q0 * nt * acq.nrec;
+        A.refl = A2.refl = born_refl;
+        A.rec_out = A2.rec_out = born_out + (size_t)q0 * nt * acq.nrec;
         if ((rc = mark())) return rc;
         rc = run_phase(ctx, graph, st, [&]() -> int {
-          for (int n = 0; n < nt; ++n) {
-            StepRT r{};
-            r.n = n;
-            r.snap_idx = r.max_idx = -1;
-            r.img_idx = inK(n + 1) ? (n + 1) / isnap - 1 : -1;
-            const int r2 = step1(ctx, MODE_BORN, A, F, r, nb, st);
+          auto slot = [&](int k) { return inK(k) ? k / isnap - 1 : -1; };
+          for (int n = 0; n < nt;) {
+            int r2;
+            if (two && n + 2 <= nt) {
+              Step2RT r;
+              r.t1 = n;
+              r.t2 = n + 1;
+              r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+              r.img_mid_idx = slot(n + 1);
+              r.img_out_idx = slot(n + 2);
+              r.dmax_flag = 0;
+              r2 = step2(ctx, MODE_BORN, A2, C, F, r, nb, st);
+              n += 2;
+            } else {
+              StepRT r{};
+              r.n = n;
+              r.snap_idx = r.max_idx = -1;
+              r.img_idx = slot(n + 1);
+              r2 = step1(ctx, MODE_BORN, A, F, r, nb, st);
+              n += 1;
+            }
             if (r2) return r2;
             ++step_launches;
           }

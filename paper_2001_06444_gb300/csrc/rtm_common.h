@@ -104,6 +104,7 @@ struct Step2Args {
   float *num, *den;
   unsigned *dmax;
   int *err;                      // set to 1 if a bounded wait gave up
+  const float *refl;             // [nz][nx] reflectivity of the Born operator
 };
 
 struct Step2RT {
@@ -112,8 +113,9 @@ struct Step2RT {
   int snap_mid_idx;    // store the intermediate field (FP32 only)
   int snap_out_idx;    // store the output field (FP32 only)
   int max_out_idx;     // reduce max |output| into this scale slot (half precision)
-  int img_mid_idx;     // image with the intermediate field (backward)
-  int img_out_idx;     // image with the output field (backward)
+  int img_mid_idx;     // image with the intermediate field (backward); Born:
+                       // inject c m S from this snapshot at substep 1
+  int img_out_idx;     // image with the output field (backward); Born: at substep 2
   int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
 };
 

@@ -228,6 +228,25 @@ __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, co
   return make_float4(out[0], out[1], out[2], out[3]);
 }
 
+// Born modelling: d += (c m) S at the physical pixels of a 4-column strip
+// (row i, columns j0..j0+3; j0 a multiple of 4) from snapshot idx; the same
+// rounding as the single-step kernel.
+__device__ __forceinline__ float4 born_inject4(const Step2Args &A, int b, int idx, int i, int j0,
+                                               float4 d, const float4 &c) {
+  const Geo &g = A.g;
+  if (idx < 0 || i < 0 || i >= g.nz || j0 < 0 || j0 >= g.SX) return d;
+  float sdq, inv;
+  snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + idx], sdq, inv);
+  const float4 S = snap_load4(A.snap, ((long long)b * A.nsnap + idx) * g.pplane +
+                                          (long long)i * g.SX + j0, A.snap_dtype, sdq);
+  const float *m = A.refl + (long long)i * g.nx + j0;
+  if (j0 < g.nx) d.x = fmaf(c.x * __ldg(m), S.x, d.x);
+  if (j0 + 1 < g.nx) d.y = fmaf(c.y * __ldg(m + 1), S.y, d.y);
+  if (j0 + 2 < g.nx) d.z = fmaf(c.z * __ldg(m + 2), S.z, d.z);
+  if (j0 + 3 < g.nx) d.w = fmaf(c.w * __ldg(m + 3), S.w, d.w);
+  return d;
+}
+
 }  // namespace
 
 template <int MODE>
@@ -334,7 +353,9 @@ __global__ void __launch_bounds__(NTH, 3)
       const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
       const int grow = min(max(z0 - 4 + er, 0), g.NZ - 1);
       const float gzr = interior ? 1.f : A.gz[grow];
-      const float4 nd = update4(&zc[r], xl, xr, dv, cv, A.k, interior, gzr, A.gx, gcol, g.P);
+      float4 nd = update4(&zc[r], xl, xr, dv, cv, A.k, interior, gzr, A.gx, gcol, g.P);
+      if (MODE == MODE_BORN)
+        nd = born_inject4(A, b, rt.img_mid_idx, z0 - 4 + er - g.nb, gcol - g.CP, nd, cv);
       const float4 ce = zc[r + 4];
       *reinterpret_cast<float4 *>(&S.d[er][4 * tx]) = nd;
       *reinterpret_cast<float4 *>(&S.v1[er][4 * tx]) =
@@ -348,7 +369,7 @@ __global__ void __launch_bounds__(NTH, 3)
   // rounding order as the single-step kernel)
   {
     const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
-    if (MODE != MODE_BWD) {
+    if (MODE == MODE_FWD || MODE == MODE_MODEL) {
       const int sr = A.src_row[shot] - (z0 - 4), sc = A.src_col[shot] - (x0 - 4);
       if (sr >= 0 && sr < EZ && sc >= 0 && sc < EX) {  // block-uniform
         if (tid == 0) {
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(NTH, 3)
         }
         __syncthreads();
       }
-    } else {
+    } else if (MODE == MODE_BWD) {
       const int p0 = A.rext_ptr[tile], p1 = A.rext_ptr[tile + 1];
       if (p1 > p0) {  // block-uniform
         const float *dsamp = A.seis + ((long long)shot * A.nt + rt.t1) * A.nrec;
@@ -378,7 +399,7 @@ __global__ void __launch_bounds__(NTH, 3)
   }
 
   // step-(n+1) work on the centre: recording, FP32 snapshot, imaging
-  if (MODE == MODE_MODEL) {
+  if (MODE == MODE_MODEL || MODE == MODE_BORN) {
     const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
     const int p0 = A.rcen_ptr[tile], p1 = A.rcen_ptr[tile + 1];
     float *ro = A.rec_out + ((long long)b * A.nt + rt.t1) * A.nrec;
@@ -453,6 +474,8 @@ __global__ void __launch_bounds__(NTH, 3)
       const int grow = min(max(z0 + 3 * ty + r, 0), g.NZ - 1);
       const float gzr = interior ? 1.f : A.gz[grow];
       res[r] = update4(&zc[r], xl, xr, dv, cv, A.k, interior, gzr, A.gx, gcol, g.P);
+      if (MODE == MODE_BORN)
+        res[r] = born_inject4(A, b, rt.img_out_idx, z0 + 3 * ty + r - g.nb, gcol - g.CP, res[r], cv);
       cen[r] = zc[r + 4];
     }
   }
@@ -462,7 +485,7 @@ __global__ void __launch_bounds__(NTH, 3)
     const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
     bool stage = false;
     int sr = -1, sc = -1, p0 = 0, p1 = 0;
-    if (MODE != MODE_BWD) {
+    if (MODE == MODE_FWD || MODE == MODE_MODEL) {
       sr = A.src_row[shot] - z0;
       sc = A.src_col[shot] - x0;
       if (sr >= 0 && sr < C2Z && sc >= 0 && sc < C2X)
@@ -483,10 +506,10 @@ __global__ void __launch_bounds__(NTH, 3)
           *reinterpret_cast<float4 *>(&S.d[4 + 3 * ty + r][4 + 4 * tx]) = res[r];
       }
       __syncthreads();
-      if (MODE != MODE_BWD) {
+      if (MODE == MODE_FWD || MODE == MODE_MODEL) {
         if (sr >= 0 && tid == 0)
           S.d[4 + sr][4 + sc] += S.c[4 + sr][4 + sc] * (A.wav[rt.t2] * A.src_scale);
-      } else {
+      } else if (MODE == MODE_BWD) {
         const float *dsamp = A.seis + ((long long)shot * A.nt + rt.t2) * A.nrec;
         for (int e = p0 + tid; e < p1; e += NTH) {
           const int2 en = A.rcen_ent[e];
@@ -494,7 +517,7 @@ __global__ void __launch_bounds__(NTH, 3)
         }
       }
       __syncthreads();
-      if (MODE == MODE_MODEL) {
+      if (MODE == MODE_MODEL || MODE == MODE_BORN) {
         float *ro = A.rec_out + ((long long)b * A.nt + rt.t2) * A.nrec;
         for (int e = p0 + tid; e < p1; e += NTH) {
           const int2 en = A.rcen_ent[e];
@@ -604,7 +627,7 @@ int step2_ext() { return 4; }
 cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                          cudaStream_t st) {
-  static bool attr_set[3] = {false, false, false};
+  static bool attr_set[4] = {false, false, false, false};
   const size_t smem = step2_smem_bytes();
   dim3 grid(A.g.ntx2, A.g.ntz2, B), block(32, NTH / 32);
   cudaError_t e = cudaSuccess;
@@ -620,6 +643,12 @@ cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
       attr_set[1] = e == cudaSuccess;
     }
     if (e == cudaSuccess) k_step2<MODE_MODEL><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
+  } else if (mode == MODE_BORN) {
+    if (!attr_set[3]) {
+      e = cudaFuncSetAttribute(k_step2<MODE_BORN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr_set[3] = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) k_step2<MODE_BORN><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
   } else {
     if (!attr_set[2]) {
       e = cudaFuncSetAttribute(k_step2<MODE_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -91,3 +91,31 @@ def test_born_refuses_checkpoint_mode(ctx, problem):
         ctx.born(rtm.make_grid(*s.grid_tuple()), vm, acq, refl, rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0, 80),
                  out)
     assert ei.value.code == rtm.RTM_ERR_ARG
+
+
+def test_two_step_born_matches_single_step_bitwise(ctx, problem):
+    """The two-step kernel injects c m S in both substeps (its extended ring
+    included) with the single-step kernel's rounding: the data agree bit for
+    bit, for even and odd isnap, odd nt and half-precision snapshots."""
+    import os
+
+    s, vm, refl = problem
+    s = inputs.Survey(s.nx, s.nz, s.nb, s.dx, s.dz, s.dt, 301, s.vel, s.src_ix, s.src_iz,
+                      s.rec_ix, s.rec_iz, s.wavelet[:301])
+    old = os.environ.get("RTM_STEP_KERNEL")
+    os.environ["RTM_STEP_KERNEL"] = "1"
+    try:
+        one = rtm.Context(0)
+    finally:
+        if old is None:
+            del os.environ["RTM_STEP_KERNEL"]
+        else:
+            os.environ["RTM_STEP_KERNEL"] = old
+    try:
+        for isnap, mode in ((4, rtm.SNAP_F32), (3, rtm.SNAP_F32), (1, rtm.SNAP_F32),
+                            (4, rtm.SNAP_F16), (2, rtm.SNAP_BF16)):
+            a = _gpu(one, s, vm, refl, isnap, dtype=mode)
+            b = _gpu(ctx, s, vm, refl, isnap, dtype=mode)
+            assert np.array_equal(a, b), (isnap, mode)
+    finally:
+        one.close()
