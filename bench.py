@@ -265,12 +265,15 @@ def run_native(args, world, rank, local):
         ctx.migrate(grid, h_vel, acq, h_seis, opts, h_img)
         barrier(world)
         t = time.perf_counter()
+        calls = []
         for _ in range(args.steps):
+            c0 = time.perf_counter()
             ctx.migrate(grid, h_vel, acq, h_seis, opts, h_img)
+            calls.append(round(time.perf_counter() - c0, 4))
         dt = max_over_ranks(time.perf_counter() - t, world)
         e2e = {"value": shots / dt, "unit": "shots/s",
                "h2d_bytes_per_step": int(h_seis.numel() * 4 + h_vel.numel() * 4),
-               "d2h_bytes_per_step": int(h_img.numel() * 4)}
+               "d2h_bytes_per_step": int(h_img.numel() * 4), "call_s": calls}
         del h_seis
 
     cpu = None
