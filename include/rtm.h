@@ -229,6 +229,18 @@ int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample,
 int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,
              const float *refl, const rtm_opts *opts, float *seis, void *stream);
 
+/* The adjoint of rtm_born (the gradient operator of least-squares
+ * migration): the imaging numerator of Eq. 5, sum over the shots of sum over
+ * the imaging steps of S^k w^k, with no illumination normalisation and no
+ * Laplacian filter (opts->eps and opts->laplacian are not used).  Same
+ * arguments and checks as rtm_migrate; image [nz][nx].  With the same grid,
+ * velocity, acquisition and options, <rtm_born(m), d> = <m,
+ * rtm_migrate_adjoint(d)> up to FP32 rounding, in every snapshot format
+ * (both read the same stored snapshots). */
+int rtm_migrate_adjoint(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
+                        const rtm_acq *acq, const float *seis, const rtm_opts *opts, float *image,
+                        void *stream);
+
 /* Per-pixel statistics of n images (§2.3; stage 3 of §3): mean and standard
  * deviation (divisor n-1; 0 when n == 1) reduced in FP64, and the 5% and 95%
  * quantiles (linear interpolation between order statistics at h = (n-1) p).

@@ -1226,9 +1226,11 @@ int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_ac
   return rc;
 }
 
+// raw: the stacked imaging numerator (no illumination normalisation, no
+// filter), the adjoint of Born modelling.
 static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const float *vels,
                           const rtm_acq *acq, const float *seis, const rtm_opts *opts,
-                          float *images, void *stream) {
+                          float *images, void *stream, bool raw = false) {
   if (!ctx) return RTM_ERR_ARG;
   int rc;
   if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true)) ||
@@ -1240,12 +1242,17 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   cudaStream_t st = (cudaStream_t)stream;
   const size_t vbytes = (size_t)nsample * grid->nx * grid->nz * 4;
   const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
-  const MigrationPlan plan = plan_migration(*grid, *acq, *opts, nsample);
+  rtm_opts op = *opts;
+  if (raw) {
+    op.eps = -1.0;  // the stacking kernel adds num as it is
+    op.laplacian = 0;
+  }
+  const MigrationPlan plan = plan_migration(*grid, *acq, op, nsample);
   const size_t io = (is_device_ptr(vels) ? 0 : vbytes) + (is_device_ptr(seis) ? 0 : sbytes) +
                     (is_device_ptr(images) ? 0 : vbytes);
   const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
   const long long nitems = (long long)nsample * acq->nshot;
-  const RunConfig cfg = config_for(ctx, *grid, *opts);
+  const RunConfig cfg = config_for(ctx, *grid, op);
   size_t want = plan.shared_bytes + io + (size_t)nitems * plan.item_bytes;
   const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
   if (cap > 0) want = std::min(want, plan.shared_bytes + io + (size_t)cap * plan.item_bytes);
@@ -1264,7 +1271,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
   if (!rc) rc = view_in(ctx, s, seis, sbytes, st);
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
-  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, *opts, im.d, B, st, cfg);
+  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, op, im.d, B, st, cfg);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
   if (!rc && (im.staged || ctx->prof)) rc = check_wait_flag(ctx);  // the stream was synchronised
   unreserve(ctx, got);
@@ -1280,6 +1287,12 @@ int rtm_migrate_ensemble(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const 
                          const rtm_acq *acq, const float *seis, const rtm_opts *opts,
                          float *images, void *stream) {
   return migrate_common(ctx, grid, nsample, vels, acq, seis, opts, images, stream);
+}
+
+int rtm_migrate_adjoint(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
+                        const rtm_acq *acq, const float *seis, const rtm_opts *opts, float *image,
+                        void *stream) {
+  return migrate_common(ctx, grid, 1, vel, acq, seis, opts, image, stream, true);
 }
 
 int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,

@@ -41,7 +41,8 @@ __global__ void k_norm_stack(float *num, float *den, const unsigned *dmax,
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const float dd = dv[l] + add;
-      const float img = dd > 0.f ? nv[l] / dd : 0.f;
+      // eps < 0: the numerator as it is (the adjoint of Born modelling)
+      const float img = eps < 0.f ? nv[l] : (dd > 0.f ? nv[l] / dd : 0.f);
       const float y = img - c[l];
       const float t = a[l] + y;
       c[l] = (t - a[l]) - y;

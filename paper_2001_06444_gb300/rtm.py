@@ -27,7 +27,8 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 # every entry point the header declares
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
-           "rtm_migrate_ensemble", "rtm_born", "rtm_ensemble_stats", "rtm_uncertainty_maps",
+           "rtm_migrate_ensemble", "rtm_born", "rtm_migrate_adjoint", "rtm_ensemble_stats",
+           "rtm_uncertainty_maps",
            "rtm_submit", "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
            "rtm_compress", "rtm_decompress", "rtm_eikonal", "rtm_last_error", "rtm_cfl_limit")
 
@@ -95,6 +96,8 @@ def lib():
                                                C.POINTER(Opts), vp, vp]
             L.rtm_born.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Acq), vp, C.POINTER(Opts), vp,
                                    vp]
+            L.rtm_migrate_adjoint.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Acq), vp,
+                                              C.POINTER(Opts), vp, vp]
             L.rtm_ensemble_stats.argtypes = [vp, vp, ip, C.c_long, vp, vp, vp, vp, vp]
             L.rtm_uncertainty_maps.argtypes = [vp, vp, vp, C.c_long, vp, vp, vp]
             L.rtm_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
@@ -304,6 +307,16 @@ class Context:
         self._check(lib().rtm_born(self.h, C.byref(grid), ptrs[0], C.byref(acq), ptrs[1],
                                    C.byref(opts), ptrs[2], _stream(vel, refl, seis)))
         return seis
+
+    def migrate_adjoint(self, grid: Grid, vel, acq: Acq, seis, opts: Opts, image):
+        """The adjoint of born: the stacked imaging numerator of seis
+        [nshot][nt][nrec] into image [nz][nx] (float32, host or device)."""
+        for a in (vel, seis, image):
+            _check_dtype(a, "float32")
+        ptrs = [C.c_void_p(_ptr(a)[0]) for a in (vel, seis, image)]
+        self._check(lib().rtm_migrate_adjoint(self.h, C.byref(grid), ptrs[0], C.byref(acq), ptrs[1],
+                                              C.byref(opts), ptrs[2], _stream(vel, seis, image)))
+        return image
 
     def ensemble_stats(self, images, mean, std, q05, q95):
         _check_dtype(images, "float32")

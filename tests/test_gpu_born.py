@@ -119,3 +119,45 @@ def test_two_step_born_matches_single_step_bitwise(ctx, problem):
             assert np.array_equal(a, b), (isnap, mode)
     finally:
         one.close()
+
+
+def _adjoint(ctx, s, vm, data, isnap, dtype=rtm.SNAP_F32, checkpoint=0):
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    ctx.migrate_adjoint(rtm.make_grid(*s.grid_tuple()), torch.from_numpy(vm).cuda(), acq,
+                        torch.from_numpy(data).cuda(), rtm.Opts(isnap, dtype, 1e-6, 1, checkpoint),
+                        img)
+    torch.cuda.synchronize()
+    return img.cpu().numpy()
+
+
+def test_adjoint_matches_oracle_numerator(ctx, problem):
+    # the oracle's per-shot numerators (no normalisation, no filter), summed
+    s, vm, refl = problem
+    data = _oracle(s, vm, refl, 4).astype(np.float32)
+    g = oracle.grid(*s.grid_tuple())
+    w = s.wavelet.astype(np.float32).astype(np.float64)
+    _, num, _ = oracle.migrate(g, vm.astype(np.float64), s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, w,
+                               data.astype(np.float64), isnap=4, return_parts=True)
+    want = num.sum(axis=0)
+    assert rel_l2(_adjoint(ctx, s, vm, data, 4), want) <= 1e-3
+    # checkpointed recomputation gives the same numerator
+    assert np.array_equal(_adjoint(ctx, s, vm, data, 4, checkpoint=40), _adjoint(ctx, s, vm, data, 4))
+
+
+@pytest.mark.parametrize("isnap,dtype", [(4, rtm.SNAP_F32), (3, rtm.SNAP_F32), (4, rtm.SNAP_F16)])
+def test_dot_product_born_against_adjoint(ctx, problem, isnap, dtype):
+    """<born(m), d> = <m, adjoint(d)> for a random m and random data d.  Both
+    sides are FP32 propagations of the same operator pair; their rounding
+    errors are independent, relative ~1e-6 per field, so the two inner
+    products agree to about that: the test allows 1e-4 of their size."""
+    s, vm, _ = problem
+    m = (inputs.normal(61, s.nz * s.nx).reshape(s.nz, s.nx) * 0.05).astype(np.float32)
+    d = (inputs.normal(62, len(s.src_ix) * s.nt * len(s.rec_ix))
+         .reshape(len(s.src_ix), s.nt, len(s.rec_ix)) * 1e-3).astype(np.float32)
+    bm = _gpu(ctx, s, vm, m, isnap, dtype=dtype)
+    ad = _adjoint(ctx, s, vm, d, isnap, dtype=dtype)
+    lhs = float(np.dot(bm.ravel().astype(np.float64), d.ravel().astype(np.float64)))
+    rhs = float(np.dot(m.ravel().astype(np.float64), ad.ravel().astype(np.float64)))
+    assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), abs(rhs)), (lhs, rhs)
