@@ -371,3 +371,32 @@ def test_full_size_ensemble_sampled_parity(ctx):
     assert np.allclose(std, sd, rtol=1e-12, atol=1e-13 * np.abs(sd).max())
     assert np.array_equal(q05, a.astype(np.float32))
     assert np.array_equal(q95, b.astype(np.float32))
+
+
+def test_velocity_ensemble_uncertainty_maps(ctx):
+    """The uncertainty maps of the velocity samples themselves (the paper
+    maps the std, confidence index and ratio of its velocity ensemble as
+    well as of its images): 64 GRF samples of the full-size model, statistics
+    and Eq. 6 / Eq. 7 maps on the GPU against the oracle's on the same samples."""
+    s = inputs.full_size(nshot=1)
+    ens = f32(inputs.ensemble(inputs.smooth(s.vel, s.dx, s.dz, 60.0), s.dx, s.dz, 64))
+    npix = s.nz * s.nx
+    x = torch.from_numpy(ens.reshape(64, npix)).cuda()
+    out = [torch.zeros(npix, dtype=t, device="cuda")
+           for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    ctx.ensemble_stats(x, *out)
+    c = torch.zeros(npix, dtype=torch.float64, device="cuda")
+    r = torch.zeros(npix, dtype=torch.float64, device="cuda")
+    ctx.uncertainty_maps(out[0], out[1], c, r)
+    torch.cuda.synchronize()
+    m, sd, a, b = oracle.ensemble_stats(ens.reshape(64, npix))
+    assert np.allclose(out[0].cpu().numpy(), m, rtol=1e-12)
+    assert np.allclose(out[1].cpu().numpy(), sd, rtol=1e-10, atol=1e-9)
+    assert np.array_equal(out[2].cpu().numpy(), a.astype(np.float32))
+    assert np.array_equal(out[3].cpu().numpy(), b.astype(np.float32))
+    oc, orr = oracle.uncertainty_maps(out[0].cpu().numpy(), out[1].cpu().numpy())
+    assert np.allclose(c.cpu().numpy(), oc, rtol=1e-14, atol=1e-15)
+    assert np.allclose(r.cpu().numpy(), orr, rtol=1e-14, atol=0)
+    # the water layer is not perturbed: zero std, confidence 1 there
+    assert np.all(out[1].cpu().numpy().reshape(s.nz, s.nx)[:40] == 0.0)
+    assert np.all(c.cpu().numpy().reshape(s.nz, s.nx)[:40] == 1.0)
