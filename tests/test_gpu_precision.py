@@ -6,7 +6,7 @@ rtm_ensemble_stats) against the FP64 oracle with the same quantisation
 replayed, and against exact snapshots.
 
 Sizes are scaled down from the 1701 x 351 x 5000 ensemble so that the
-oracle finishes in seconds: 8 samples of a layered model (201 x 101 cells at
+oracle finishes in seconds: 16 samples of a layered model (201 x 101 cells at
 10 m, 4 % Gaussian-random-field perturbation, water fixed) x 2 shots x 800
 steps.
 """
@@ -20,7 +20,7 @@ from paper_2001_06444_gb300 import inputs, rtm
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-NS, NX, NZ, NT = 8, 201, 101, 800
+NS, NX, NZ, NT = 16, 201, 101, 800
 IMG_TOL = {rtm.SNAP_F32: 1e-3, rtm.SNAP_BF16: 1e-2, rtm.SNAP_F16: 1e-2}
 STD_TOL = 2e-2
 
