@@ -71,6 +71,14 @@ __host__ __device__ constexpr int perm(int i) {
        : i == 12 ? 10 : i == 13 ? 11 : i == 14 ? 14 : 15;
 }
 
+// perm(i) for a run-time i: the 16 values as nibbles of one constant
+constexpr u64 kPermPack = 0xfebad976c8532410ull;
+__host__ __device__ constexpr bool perm_pack_ok(int i = 0) {
+  return i == 16 || ((int)((kPermPack >> (4 * i)) & 15u) == perm(i) && perm_pack_ok(i + 1));
+}
+static_assert(perm_pack_ok(), "packed coefficient order");
+__device__ __forceinline__ int perm_rt(int i) { return (int)((kPermPack >> (4 * i)) & 15u); }
+
 struct EncArgs {
   const float *data;
   long long n0, n1;
@@ -537,9 +545,9 @@ __device__ __forceinline__ int zeros(R &rd, int lim) {
 
 // Parse one block.  FULL: reconstruct it into x; else only move past it.
 // Returns false on a malformed block.
-template <bool LL, bool FULL, class R>
+template <bool LL, bool FULL, class R, class Q = int>
 __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, unsigned char *sfx,
-                                            int sstride, float (&x)[16]) {
+                                            Q *qs, int sstride, float (&x)[16]) {
   constexpr int Ktop = LL ? 32 : 30;
   if (!getbits(rd, 1)) {
     if (FULL) {
@@ -591,31 +599,58 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
     found |= 1u << p;
     n = p + 1;
   }
-  // refinement: magnitudes and signs
+  // refinement: magnitudes and signs, in coding order.  Fixed accuracy takes
+  // a rolled loop (smaller code) through this thread's shared-memory slots
+  // qs[j * sstride], j in block order; lossless keeps the unrolled register
+  // form (its 64-bit slots would cost occupancy).
   using S = typename std::conditional<LL, long long, int>::type;
   S q[16];
-  bool wide = false;  // fixed accuracy with kmin > 26 reconstructs in 64 bits
   long long qw[16];
+  if constexpr (!LL) {
+    if (FULL) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    long long v = 0;
-    if (i < n) {
+      for (int j = 0; j < 16; ++j) qs[j * sstride] = 0;
+    }
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
       const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;  // plane of the next event
       u64 t = w > 32 ? 0ull : (u64)getbits(rd, min(w, 32));
       if ((found >> i) & 1u) t |= 1ull << w;
       if (t) {
         const bool ng = getbits(rd, 1);
-        v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
+        long long v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
         if (ng) v = -v;
+        if (FULL) qs[perm_rt(i) * sstride] = (Q)v;
       }
     }
-    if (FULL) {
-      q[perm(i)] = (S)v;
-      qw[perm(i)] = v;
+    if (!FULL) return true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      q[j] = (S)qs[j * sstride];
+      qw[j] = (long long)qs[j * sstride];
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      long long v = 0;
+      if (i < n) {
+        const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;
+        u64 t = w > 32 ? 0ull : (u64)getbits(rd, min(w, 32));
+        if ((found >> i) & 1u) t |= 1ull << w;
+        if (t) {
+          const bool ng = getbits(rd, 1);
+          v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
+          if (ng) v = -v;
+        }
+      }
+      if (FULL) {
+        q[perm(i)] = (S)v;
+        qw[perm(i)] = v;
+      }
+    }
+    if (!FULL) return true;
   }
-  if (!FULL) return true;
-  if (!LL) wide = kmin > 26;
+  const bool wide = !LL && kmin > 26;  // fixed accuracy with kmin > 26 reconstructs in 64 bits
   bool ok = true;
   if (LL || !wide) {
     // inverse transform: columns, then rows
@@ -676,7 +711,7 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
 template <bool LL>
 __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 arr,
                              const unsigned char *ktab, u32 (*offs)[33], u32 *cw, u32 *cstart,
-                             u32 *cnw, unsigned char *sfx, bool &bad) {
+                             u32 *cnw, unsigned char *sfx, int *qs, bool &bad) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 g = blockIdx.x * kDecWarps + warp;  // this warp's group of 32 chunks
   const u32 c0 = g * 32;
@@ -701,7 +736,7 @@ __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 ar
         float x[16];
         for (u32 k = 0; k < nblk && ok; ++k) {
           offs[lane][k] = (u32)(rd.pos - (u64)start * 32);
-          ok = parse_block<LL, false>(rd, ktab, sfx, kDecWarps * 32, x);
+          ok = parse_block<LL, false>(rd, ktab, sfx, qs, kDecWarps * 32, x);
         }
         ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next;
       }
@@ -723,7 +758,7 @@ __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 ar
     if (nw && b < a.nb) {
       SReader rd{cw, nw, offs[j][lane]};
       float x[16];
-      const bool ok = parse_block<LL, true>(rd, ktab, sfx, kDecWarps * 32, x) && !rd.overrun();
+      const bool ok = parse_block<LL, true>(rd, ktab, sfx, qs, kDecWarps * 32, x) && !rd.overrun();
       if (!ok) bad = true;
       const u32 bi = b / a.nb1, bj = b - bi * a.nb1;
 #pragma unroll
@@ -751,6 +786,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_cz_decode(const __grid_const
   __shared__ u32 s_cw[kDecWarps][kChunkWords + 2];
   __shared__ u32 s_start[kDecWarps][32], s_nw[kDecWarps][32];
   __shared__ unsigned char s_sfx[16][kDecWarps * 32];
+  __shared__ int s_q[LL ? 1 : 16][kDecWarps * 32];  // coefficient slots (fixed accuracy)
   __shared__ unsigned char s_kmin[kTab];
   __shared__ int s_ok;
   const u32 arr = blockIdx.y;
@@ -778,7 +814,7 @@ __global__ void __launch_bounds__(kDecWarps * 32) k_cz_decode(const __grid_const
   const int warp = threadIdx.x >> 5;
   bool bad = false;
   decode_group<LL>(a, slot, arr, s_kmin, s_offs[warp], s_cw[warp], s_start[warp], s_nw[warp],
-                   &s_sfx[0][threadIdx.x], bad);
+                   &s_sfx[0][threadIdx.x], &s_q[0][threadIdx.x], bad);
   if (bad) {
     atomicExch(a.err, 1);
     atomicMin(a.err + 1, (int)arr);
