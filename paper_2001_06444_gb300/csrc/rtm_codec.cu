@@ -710,7 +710,7 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
 
 template <bool LL>
 __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 arr,
-                             const unsigned char *ktab, u32 (*offs)[33], u32 *cw, u32 *cstart,
+                             const unsigned char *ktab, unsigned short (*offs)[33], u32 *cw, u32 *cstart,
                              u32 *cnw, unsigned char *sfx, int *qs, bool &bad) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 g = blockIdx.x * kDecWarps + warp;  // this warp's group of 32 chunks
@@ -735,7 +735,7 @@ __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 ar
         const u32 b0 = c * kChunk, nblk = min((u32)kChunk, a.nb - b0);
         float x[16];
         for (u32 k = 0; k < nblk && ok; ++k) {
-          offs[lane][k] = (u32)(rd.pos - (u64)start * 32);
+          offs[lane][k] = (unsigned short)(rd.pos - (u64)start * 32);  // < 640 words
           ok = parse_block<LL, false>(rd, ktab, sfx, qs, kDecWarps * 32, x);
         }
         ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next;
@@ -782,7 +782,7 @@ __device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 ar
 // streams, and the fixed-accuracy one reports bad headers.
 template <bool LL>
 __global__ void __launch_bounds__(kDecWarps * 32) k_cz_decode(const __grid_constant__ DecArgs a) {
-  __shared__ u32 s_offs[kDecWarps][32][33];
+  __shared__ unsigned short s_offs[kDecWarps][32][33];  // block bit offsets in a chunk
   __shared__ u32 s_cw[kDecWarps][kChunkWords + 2];
   __shared__ u32 s_start[kDecWarps][32], s_nw[kDecWarps][32];
   __shared__ unsigned char s_sfx[16][kDecWarps * 32];
