@@ -116,3 +116,30 @@ def test_cap_and_bad_inputs_are_reported(ctx):
     _check(fields.cpu().numpy()[0, 0],
            oracle.eikonal(vel.astype(np.float64), 10.0, 10.0, nz - 1, nx - 1))
     assert iters[0] >= 2
+
+
+def test_every_tile_shape_gives_the_same_bits(ctx):
+    # each tile shape updates every node from neighbours in the same state as
+    # the sequential sweep, so all shapes (and both storages) agree bit for bit
+    import os
+
+    nz, nx = 45, 67
+    vel = _model(3, nz, nx, 10.0, 12.0)[None]
+    d = torch.from_numpy(vel).cuda()
+    outs = []
+    old = os.environ.get("RTM_EIK_TILE")
+    try:
+        for shape in ("1x1", "2x2", "2x4", "4x2"):
+            os.environ["RTM_EIK_TILE"] = shape
+            for storage in ("shared", "offchip"):
+                f = torch.zeros((1, 2, nz, nx), dtype=torch.float32, device="cuda")
+                ctx.eikonal(d, 10.0, 12.0, [0, nz - 1], [5, nx // 2], fields=f, storage=storage)
+                outs.append(f.cpu().numpy().view(np.uint32))
+    finally:
+        if old is None:
+            os.environ.pop("RTM_EIK_TILE", None)
+        else:
+            os.environ["RTM_EIK_TILE"] = old
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    _check(outs[0].view(np.float32)[0, 0], oracle.eikonal(vel[0].astype(np.float64), 10.0, 12.0, 0, 5))
