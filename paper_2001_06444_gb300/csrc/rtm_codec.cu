@@ -332,6 +332,40 @@ struct Block {
     }
     bw.flush();
   }
+
+  // Fixed accuracy, the same bits with rolled loops over the events and the
+  // prefix members only (sparse blocks skip the rest): s[i] and m[i] are read
+  // back from this lane's shared-memory slots ss[i * stride], ms[i * stride].
+  __device__ __forceinline__ void emit_rolled(u32 *buf, u32 pos, const unsigned char *ss,
+                                              const u32 *ms, int stride) const {
+    static_assert(!LL, "fixed accuracy only");
+    if (zero) return;
+    BitWriter bw(buf, pos);
+    bw.put(1u | ((u32)(e + 150) << 1), 10);
+    int k = Ktop, nxt = 0;
+#pragma unroll 1
+    for (u32 b = ev; b; b &= b - 1u) {
+      const int i = __ffs(b) - 1;
+      const int si = ss[i * stride];
+      bw.put(0, k - si);  // failed group tests of the planes in between (<= 30)
+      const int gap = i - nxt;
+      bw.put(1u | (1u << (gap + 1)), gap + 2);
+      nxt = i + 1;
+      k = si;
+    }
+    if (cur < 16) bw.put(0, k - kmin + 1);  // <= 31
+#pragma unroll 1
+    for (int i = 0; i < cur; ++i) {
+      const int w = ss[i * stride] - kmin;  // <= 30
+      const u32 t = ms[i * stride] >> kmin;
+      const u32 field = t & ((1u << w) - 1u);
+      if ((nz >> i) & 1u)
+        bw.put(field | (((neg >> i) & 1u) << w), w + 1);
+      else
+        bw.put(0, w);
+    }
+    bw.flush();
+  }
 };
 
 // Pass 1: code one tile (256 blocks, 8 chunks) into its staging slot of
@@ -341,6 +375,8 @@ __global__ void __launch_bounds__(kTile, LL ? 2 : 3) k_cz_encode(const __grid_co
   __shared__ u32 sbuf[kWarps][kChunkWords];
   __shared__ u32 s_words[kWarps];
   __shared__ unsigned char s_kmin[kTab];
+  __shared__ unsigned char s_s[LL ? 1 : 16][kTile];  // entry planes (fixed accuracy)
+  __shared__ u32 s_m[LL ? 1 : 16][kTile];            // magnitudes (fixed accuracy)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kTab; i += blockDim.x) s_kmin[i] = a.kmin[i];
   __syncthreads();
@@ -379,7 +415,23 @@ __global__ void __launch_bounds__(kTile, LL ? 2 : 3) k_cz_encode(const __grid_co
   for (u32 i = lane; i < nw; i += 32) buf[i] = 0;
   if (lane == 0) s_words[warp] = nw;
   __syncwarp();
-  if (c.len) c.emit(buf, (u32)(incl - c.len));
+  // fixed accuracy: warps of dense blocks keep the unrolled emission, the
+  // others take the rolled loops (the vote is warp-uniform)
+  const bool dense = LL || __all_sync(0xffffffffu, c.len == 0 || c.zero || c.cur >= 12);
+  if (c.len) {
+    if (dense) {
+      c.emit(buf, (u32)(incl - c.len));
+    } else if constexpr (!LL) {
+      if (!c.zero) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          s_s[i][threadIdx.x] = (unsigned char)max(c.s[i], 0);
+          s_m[i][threadIdx.x] = c.m[i];
+        }
+      }
+      c.emit_rolled(buf, (u32)(incl - c.len), &s_s[0][threadIdx.x], &s_m[0][threadIdx.x], kTile);
+    }
+  }
   const int nf = __syncthreads_or(c.nonfinite);
   u32 off = 0;
   for (int w = 0; w < warp; ++w) off += s_words[w];
