@@ -53,10 +53,12 @@ def parse():
     p.add_argument("--nt", type=int, default=5000)
     # other workloads of the method, each printing its own JSON line
     p.add_argument("--workload", default="migrate",
-                   choices=["migrate", "ensemble", "serve", "codec", "eikonal", "stats", "born"])
+                   choices=["migrate", "ensemble", "serve", "codec", "eikonal", "stats", "born",
+                            "lsrtm"])
     p.add_argument("--samples", type=int, default=64, help="ensemble: velocity samples")
     p.add_argument("--requests", type=int, default=64, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=0.0, help="serve: arrivals/s (0 = 0.8 x capacity)")
+    p.add_argument("--iters", type=int, default=2, help="lsrtm: CGLS iterations per step")
     p.add_argument("--serve-snap", default="f16", choices=["f16", "bf16"],
                    help="serve: snapshot format of the batched, served form")
     return p.parse_args()
@@ -783,6 +785,50 @@ def run_born(args, local):
     ctx.close()
 
 
+def run_lsrtm(args, local):
+    """Least-squares migration of the full-size survey: --iters CGLS
+    iterations (one Born modelling and one adjoint migration each, plus the
+    first adjoint) over --shots shots, data = Born data of the relative
+    contrast between the true and the 60 m smoothed model (modelled untimed),
+    FP32 snapshots every 4 steps; CUDA events around --steps solves after
+    --warmup."""
+    import torch
+
+    from paper_2001_06444_gb300 import inputs, rtm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = inputs.full_size(nshot=args.shots, nt=args.nt)
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0)
+    refl = ((s.vel - vm) / s.vel).astype(np.float32)
+    grid = rtm.make_grid(*s.grid_tuple())
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    opts = rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0, 0)
+    ctx = rtm.Context(local)
+    vel = torch.from_numpy(vm.astype(np.float32)).to(dev)
+    seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
+    ctx.born(grid, vel, acq, torch.from_numpy(refl).to(dev), opts, seis)  # the data, untimed
+    out = torch.empty((s.nz, s.nx), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.lsrtm(grid, vel, acq, seis, opts, args.iters, out)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        mis = ctx.lsrtm(grid, vel, acq, seis, opts, args.iters, out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({
+        "workload": f"lsrtm_1701x351_{s.nshot}shots_nt{s.nt}_{args.iters}iters_f32snap",
+        "s_per_solve": ms / 1e3, "s_per_iteration": ms / 1e3 / (args.iters + 0.5),
+        "operator_shots_per_s": s.nshot * (2 * args.iters + 1) / (ms / 1e3),
+        "misfit_ratio": mis[-1] / mis[0], "misfits": mis, "data": "synthetic"}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -800,6 +846,8 @@ def main():
         run_stats(args, local)
     elif args.workload == "born":
         run_born(args, local)
+    elif args.workload == "lsrtm":
+        run_lsrtm(args, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:

@@ -241,6 +241,22 @@ int rtm_migrate_adjoint(rtm_ctx *ctx, const rtm_grid *grid, const float *vel,
                         const rtm_acq *acq, const float *seis, const rtm_opts *opts, float *image,
                         void *stream);
 
+/* Least-squares migration: the reflectivity m [nz][nx] that minimises
+ * ||B m - d||^2 over niter iterations of conjugate gradients on the normal
+ * equations (CGLS), starting from m = 0, with B = rtm_born and B^T =
+ * rtm_migrate_adjoint under the same grid, velocity, acquisition and
+ * options.  This is the least-squares counterpart of the migration of §2.2
+ * (Eq. 5 is one application of B^T followed by a normalisation).  Each
+ * iteration costs one Born modelling and one adjoint migration; vector
+ * updates and inner products run on the device (FP64 inner products, fixed
+ * order).  seis [nshot][nt][nrec] and refl: host or device.  misfit (host,
+ * nullable, niter + 1 values) receives ||d - B m_k||^2 after k iterations.
+ * opts->checkpoint must be 0.  Stops early (filling misfit) if the
+ * gradient vanishes.  Synchronises the stream. */
+int rtm_lsrtm(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq *acq,
+              const float *seis, const rtm_opts *opts, int niter, float *refl, double *misfit,
+              void *stream);
+
 /* Per-pixel statistics of n images (§2.3; stage 3 of §3): mean and standard
  * deviation (divisor n-1; 0 when n == 1) reduced in FP64, and the 5% and 95%
  * quantiles (linear interpolation between order statistics at h = (n-1) p).

@@ -27,7 +27,8 @@ _NAMES = {0: "RTM_OK", 1: "RTM_ERR_ARG", 2: "RTM_ERR_CFL", 3: "RTM_ERR_NOMEM",
 # every entry point the header declares
 EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_set_profiling",
            "rtm_ctx_stats", "rtm_plan_bytes", "rtm_autotune", "rtm_model", "rtm_migrate",
-           "rtm_migrate_ensemble", "rtm_born", "rtm_migrate_adjoint", "rtm_ensemble_stats",
+           "rtm_migrate_ensemble", "rtm_born", "rtm_migrate_adjoint", "rtm_lsrtm",
+           "rtm_ensemble_stats",
            "rtm_uncertainty_maps",
            "rtm_submit", "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
            "rtm_compress", "rtm_decompress", "rtm_eikonal", "rtm_last_error", "rtm_cfl_limit")
@@ -98,6 +99,8 @@ def lib():
                                    vp]
             L.rtm_migrate_adjoint.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Acq), vp,
                                               C.POINTER(Opts), vp, vp]
+            L.rtm_lsrtm.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Acq), vp, C.POINTER(Opts),
+                                    ip, vp, C.POINTER(C.c_double), vp]
             L.rtm_ensemble_stats.argtypes = [vp, vp, ip, C.c_long, vp, vp, vp, vp, vp]
             L.rtm_uncertainty_maps.argtypes = [vp, vp, vp, C.c_long, vp, vp, vp]
             L.rtm_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
@@ -317,6 +320,19 @@ class Context:
         self._check(lib().rtm_migrate_adjoint(self.h, C.byref(grid), ptrs[0], C.byref(acq), ptrs[1],
                                               C.byref(opts), ptrs[2], _stream(vel, seis, image)))
         return image
+
+    def lsrtm(self, grid: Grid, vel, acq: Acq, seis, opts: Opts, niter: int, refl):
+        """Least-squares migration (CGLS over born / migrate_adjoint): the
+        reflectivity into refl [nz][nx]; returns the misfits
+        ||d - B m_k||^2, k = 0..niter."""
+        for a in (vel, seis, refl):
+            _check_dtype(a, "float32")
+        mis = (C.c_double * (int(niter) + 1))()
+        ptrs = [C.c_void_p(_ptr(a)[0]) for a in (vel, seis, refl)]
+        self._check(lib().rtm_lsrtm(self.h, C.byref(grid), ptrs[0], C.byref(acq), ptrs[1],
+                                    C.byref(opts), int(niter), ptrs[2], mis,
+                                    _stream(vel, seis, refl)))
+        return list(mis)
 
     def ensemble_stats(self, images, mean, std, q05, q95):
         _check_dtype(images, "float32")
