@@ -564,7 +564,7 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
                    int B, cudaStream_t st, const RunConfig &cfg, const float *born_refl,
-                   float *born_out) {
+                   float *born_out, LateCopy *late) {
   Common C;
   int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel);
   if (rc) return rc;
@@ -621,6 +621,39 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     CU(cudaEventCreate(&e));
     CU(cudaEventRecord(e, st));
     ev.push_back(e);
+    return RTM_OK;
+  };
+
+  // the late seismogram upload: issued once, behind the first forward phase
+  // (outside any graph capture), in per-batch pieces in shot order; batch bi
+  // waits for its piece, and so for every earlier one, before backward steps
+  auto issue_late = [&](long long bi) -> int {
+    if (!late) return RTM_OK;
+    if (!late->issued) {
+      late->issued = true;
+      CU(cudaStreamWaitEvent(late->cs, late->alloc_done, 0));
+      const char *src = static_cast<const char *>(late->src);
+      char *dst = static_cast<char *>(late->dst);
+      int done = 0;  // shots uploaded so far
+      for (long long q0 = 0; q0 < nitems; q0 += B) {
+        const long long q1 = std::min<long long>(nitems, q0 + B);
+        // shots this batch reads (items in (sample, shot) order; a batch
+        // that crosses a sample boundary may read any shot)
+        const int hi = (q1 - 1) / acq.nshot > q0 / acq.nshot ? acq.nshot
+                                                            : (int)((q1 - 1) % acq.nshot) + 1;
+        if (hi > done) {
+          CU(cudaMemcpyAsync(dst + done * late->shot_bytes, src + done * late->shot_bytes,
+                             (size_t)(hi - done) * late->shot_bytes, cudaMemcpyHostToDevice,
+                             late->cs));
+          done = hi;
+        }
+        cudaEvent_t e;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        late->ready.push_back(e);
+        CU(cudaEventRecord(e, late->cs));
+      }
+    }
+    CU(cudaStreamWaitEvent(st, late->ready[(size_t)bi], 0));
     return RTM_OK;
   };
 
@@ -771,6 +804,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
         continue;
       }
       if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
+      if ((rc = issue_late(q0 / B))) return rc;
       if ((rc = mark())) return rc;
       rc = run_phase(ctx, graph, st, [&]() { return bwd_range(F, nt, 0, 0); });
       if (rc) return rc;
@@ -783,6 +817,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
       rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, false, true); });
       if (rc) return rc;
       if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
+      if ((rc = issue_late(q0 / B))) return rc;
       for (int sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
         const int n0 = sgi * cpC, n1 = std::min(nt, n0 + cpC), kbase = n0 / isnap;
         rc = run_phase(ctx, graph, st, [&]() -> int {
@@ -933,6 +968,29 @@ static int view_finish(rtm_ctx *ctx, View &v, float *p, size_t bytes, cudaStream
   CU(cudaMemcpyAsync(p, v.d, bytes, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   return RTM_OK;
+}
+
+static int late_begin(rtm_ctx *ctx, LateCopy &l, const void *src, void *dst, size_t shot_bytes,
+                      cudaStream_t st) {
+  l.src = src;
+  l.dst = dst;
+  l.shot_bytes = shot_bytes;
+  CU(cudaStreamCreateWithFlags(&l.cs, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&l.alloc_done, cudaEventDisableTiming));
+  CU(cudaEventRecord(l.alloc_done, st));
+  return RTM_OK;
+}
+
+// Waits on the host for whatever the upload issued (on every path, so the
+// staging buffer is never released under a copy in flight; on success the
+// copies ended before the backward phases that waited for them), then
+// releases the stream and events.
+static void late_end(LateCopy &l) {
+  if (l.issued) cudaStreamSynchronize(l.cs);
+  for (cudaEvent_t e : l.ready) cudaEventDestroy(e);
+  if (l.alloc_done) cudaEventDestroy(l.alloc_done);
+  if (l.cs) cudaStreamDestroy(l.cs);
+  l = LateCopy{};
 }
 
 static int set_device(rtm_ctx *ctx) {
@@ -1267,11 +1325,18 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   const long long nbatch = (nitems + bmax - 1) / bmax;
   const int B = (int)((nitems + nbatch - 1) / nbatch);
   View v, s, im;
+  LateCopy late;
   rc = view_in(ctx, v, vels, vbytes, st);
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
-  if (!rc) rc = view_in(ctx, s, seis, sbytes, st);
+  // host seismograms: allocate now, upload behind the first forward phase
+  if (!rc) rc = view_out(ctx, s, const_cast<float *>(seis), sbytes, st);
+  if (!rc && s.staged)
+    rc = late_begin(ctx, late, seis, s.d, (size_t)grid->nt * acq->nrec * 4, st);
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
-  if (!rc) rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, op, im.d, B, st, cfg);
+  if (!rc)
+    rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, op, im.d, B, st, cfg, nullptr,
+                        nullptr, s.staged ? &late : nullptr);
+  late_end(late);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
   if (!rc && (im.staged || ctx->prof)) rc = check_wait_flag(ctx);  // the stream was synchronised
   unreserve(ctx, got);

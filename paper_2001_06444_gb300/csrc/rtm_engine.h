@@ -94,15 +94,35 @@ int check_grid(rtm_ctx *ctx, const rtm_grid *g);
 int check_acq(rtm_ctx *ctx, const rtm_grid *g, const rtm_acq *a, bool need_rec);
 int check_opts(rtm_ctx *ctx, const rtm_opts *o);
 
+// Host seismograms whose copy to the device is issued late, on its own
+// stream: they are first read by the backward phase, so their upload runs
+// behind the first forward phase.  The copy goes in per-batch pieces in shot
+// order, each followed by an event, so a batch's backward phase waits only
+// for the shots it reads.  `alloc_done` is recorded on the main stream once
+// `dst` is allocated.
+struct LateCopy {
+  const void *src = nullptr;
+  void *dst = nullptr;
+  size_t shot_bytes = 0;  // one shot's seismogram [nt][nrec]
+  cudaStream_t cs = nullptr;
+  cudaEvent_t alloc_done = nullptr;
+  std::vector<cudaEvent_t> ready;  // one per batch, once issued
+  bool issued = false;
+};
+
 // Migration of nsample models x all shots with device pointers and a fixed
 // batch size B (items in flight).  Memory is allocated from the pool.
 // With born_refl set, Born modelling instead: the backward phase is replaced
 // by the perturbation field driven by c m S^k, recorded into born_out
-// [nitems][nt][nrec]; seis_d and img_d are not used.
+// [nitems][nt][nrec]; seis_d and img_d are not used.  With `late` set, the
+// copy of the seismograms into seis_d is issued after the first forward
+// phase is enqueued, and the main stream waits for it before any backward
+// step.
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
                    int B, cudaStream_t st, const RunConfig &cfg,
-                   const float *born_refl = nullptr, float *born_out = nullptr);
+                   const float *born_refl = nullptr, float *born_out = nullptr,
+                   LateCopy *late = nullptr);
 RunConfig config_for(rtm_ctx *ctx, const rtm_grid &gr, const rtm_opts &op);
 
 // Velocity range check (CFL of §3, positivity, finiteness); synchronises st.

@@ -69,3 +69,45 @@ def test_checkpoint_mode_single_step_kernel_and_memory():
     _, item_full = rtm.plan_bytes(g, acq, rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1, 0))
     _, item_cp = rtm.plan_bytes(g, acq, rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1, -1))
     assert item_cp < item_full / 5, (item_cp, item_full)
+
+
+@pytest.mark.parametrize("cp", [0, 26])
+def test_host_seismograms_uploaded_behind_the_forward_phase(cp):
+    """Host seismograms are uploaded on a side stream behind the first
+    forward phase; the image must equal the device-buffer image bit for bit,
+    for pinned and pageable host memory, one shot per batch (the upload is
+    issued once, in the first batch) and in checkpoint mode."""
+    s, v, seis = _problem(400)
+    opts = rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1, cp)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    with rtm.Context(0) as ctx:
+        for batch in (0, 1):
+            ctx.set_batch(batch)
+            want = _migrate(ctx, s, v, seis, opts)
+            for host in (torch.from_numpy(seis).pin_memory(), seis):
+                img = np.zeros((s.nz, s.nx), np.float32)
+                ctx.migrate(grid, v, acq, host, opts, img)
+                assert np.array_equal(img, want), (batch, cp, type(host))
+
+
+def test_host_seismograms_with_batches_across_samples():
+    """Two velocity samples x 3 shots in batches of 2: the middle batch holds
+    the last shot of sample 0 and the first of sample 1, so it waits for the
+    whole upload.  Host and device seismograms give the same images."""
+    s, v, seis = _problem(400)
+    vels = np.stack([v, (v * 1.02).astype(np.float32)])
+    opts = rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1, 0)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    with rtm.Context(0) as ctx:
+        ctx.set_batch(2)
+        want = torch.zeros((2, s.nz, s.nx), dtype=torch.float32, device="cuda")
+        ctx.migrate_ensemble(grid, torch.from_numpy(vels).cuda(), acq,
+                             torch.from_numpy(seis).cuda(), opts, want)
+        torch.cuda.synchronize()
+        got = np.zeros((2, s.nz, s.nx), np.float32)
+        ctx.migrate_ensemble(grid, vels, acq, torch.from_numpy(seis).pin_memory(), opts, got)
+        assert np.array_equal(got, want.cpu().numpy())
