@@ -50,6 +50,8 @@ struct Smem {
   float v1[EZ][EX];   // v^{n+1}
   unsigned long long bar;
   float red[NTH / 32];
+  float gxs[EX];  // sponge factors of the extended region's columns ...
+  float gzs[EZ];  // ... and rows (filled by blocks that reach the sponge)
 };
 static_assert(sizeof(float) * VX * VZ % 128 == 0, "tile offsets must stay 128-byte aligned");
 static_assert(sizeof(float) * EX * EZ % 128 == 0, "tile offsets must stay 128-byte aligned");
@@ -178,13 +180,19 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 // One leapfrog update of 4 consecutive points in difference form.
 //   zc[0..8]: the 9 rows (centre row zc[4]) of the 4-column strip,
 //   xl, xr:   the 4 columns left and right of the strip in the centre row,
-//   dv, cv:   d^n and c at the strip.
+//   dv, cv:   d^n and c at the strip,
+//   SPONGE:   the block's region reaches the sponge: every point takes the
+//             sponge form (which gives the interior formula's bits where
+//             g = 1), with gzr the row's factor and gxs the strip's four (in
+//             shared memory).  Blocks clear of the sponge compile in the
+//             interior formula alone.  (Choosing between the two forms per
+//             row measured slower.)
 // Returns d^{n+1} (before injection); v^{n+1} = v^n + d^{n+1}.  Lanes are
 // processed in pairs (0,1) and (2,3).
+template <bool SPONGE>
 __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, const float4 &xr,
                                           const float4 &dv, const float4 &cv, const Coef &k,
-                                          bool interior, float gzr, const float *gx, int col,
-                                          int P) {
+                                          float gzr, const float *gxs) {
   const float4 xc = zc[4];
   const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
   float out[4];
@@ -207,22 +215,22 @@ __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, co
     }
     const float2 c = l == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w);
     const float2 p = l == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);
-    if (interior) {
-      const float2 nd = __ffma2_rn(c, lap, p);
+    const float2 nd = __ffma2_rn(c, lap, p);
+    if (!SPONGE) {
       out[l] = nd.x;
       out[l + 1] = nd.y;
     } else {
-      const float lp[2] = {lap.x, lap.y}, cc2[2] = {c.x, c.y}, pp[2] = {p.x, p.y},
-                  cce[2] = {ce.x, ce.y};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int cc = min(max(col + l + h, 0), P - 1);
-        const float gg = gzr * gx[cc];
-        const float om = 1.f - gg;
-        // points with g == 1 take the interior formula whatever their tile
-        out[l + h] = gg == 1.f ? fmaf(cc2[h], lp[h], pp[h])
-                               : fmaf(gg * gg, pp[h], fmaf(gg * cc2[h], lp[h], -(om * om) * cce[h]));
-      }
+      // g^2 d + g c L v - (1-g)^2 v, each lane rounded as the scalar form
+      // fmaf(g g, d, fmaf(g c, L v, (-(1-g)(1-g)) v)) of the single-step
+      // kernel; points with g == 1 take the interior formula
+      const float2 gg = __fmul2_rn(make_float2(gzr, gzr),
+                                   *reinterpret_cast<const float2 *>(gxs + l));
+      const float2 om = __ffma2_rn(gg, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+      const float2 mo = __ffma2_rn(gg, make_float2(1.f, 1.f), make_float2(-1.f, -1.f));
+      const float2 w = __fmul2_rn(__fmul2_rn(om, mo), ce);
+      const float2 sp = __ffma2_rn(__fmul2_rn(gg, gg), p, __ffma2_rn(__fmul2_rn(gg, c), lap, w));
+      out[l] = gg.x == 1.f ? nd.x : sp.x;
+      out[l + 1] = gg.y == 1.f ? nd.y : sp.y;
     }
   }
   return make_float4(out[0], out[1], out[2], out[3]);
@@ -247,6 +255,87 @@ __device__ __forceinline__ float4 born_inject4(const Step2Args &A, int b, int id
   return d;
 }
 
+// Substep 1: (v^{n+1}, d^{n+1}) on the extended region, rows 4ty..4ty+3 and
+// columns 4tx..4tx+3 of it, into S.d and S.v1.
+template <int MODE, bool SPONGE>
+__device__ __forceinline__ void substep1(Smem &S, const Step2Args &A, const Step2RT &rt, int b,
+                                         int x0, int z0) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const Geo &g = A.g;
+  float4 zc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q)
+    zc[q] = *reinterpret_cast<const float4 *>(&S.v0[4 * ty + q][4 + 4 * tx]);
+  const int gcol = x0 - 4 + 4 * tx;
+  const float *gxs = &S.gxs[4 * tx];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int er = 4 * ty + r;
+    const float4 xl = *reinterpret_cast<const float4 *>(&S.v0[er + 4][4 * tx]);
+    const float4 xr = *reinterpret_cast<const float4 *>(&S.v0[er + 4][8 + 4 * tx]);
+    const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 * tx]);
+    const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
+    const float gzr = SPONGE ? S.gzs[er] : 1.f;
+    const float4 nd = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    *reinterpret_cast<float4 *>(&S.d[er][4 * tx]) = nd;
+    if (MODE != MODE_BORN) {
+      const float4 ce = zc[r + 4];
+      *reinterpret_cast<float4 *>(&S.v1[er][4 * tx]) =
+          make_float4(ce.x + nd.x, ce.y + nd.y, ce.z + nd.z, ce.w + nd.w);
+    }
+  }
+  // Born modelling: the source term joins each row's new difference, in a
+  // second pass over this thread's own rows (fewer registers live in the
+  // stencil loop), then v^{n+1} = v^n + d^{n+1}
+  if (MODE == MODE_BORN) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int er = 4 * ty + r;
+      const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
+      const float4 nd = born_inject4(A, b, rt.img_mid_idx, z0 - 4 + er - g.nb, gcol - g.CP,
+                                     *reinterpret_cast<const float4 *>(&S.d[er][4 * tx]), cv);
+      const float4 ce = zc[r + 4];
+      *reinterpret_cast<float4 *>(&S.d[er][4 * tx]) = nd;
+      *reinterpret_cast<float4 *>(&S.v1[er][4 * tx]) =
+          make_float4(ce.x + nd.x, ce.y + nd.y, ce.z + nd.z, ce.w + nd.w);
+    }
+  }
+}
+
+// Substep 2: d^{n+2} (res, before injection) and v^{n+1} (cen) on the
+// centre, rows 3ty..3ty+2 and columns 4tx..4tx+3 of it.
+template <int MODE, bool SPONGE>
+__device__ __forceinline__ void substep2(const Smem &S, const Step2Args &A, const Step2RT &rt,
+                                         int b, int x0, int z0, float4 (&res)[3],
+                                         float4 (&cen)[3]) {
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const Geo &g = A.g;
+  float4 zc[11];
+#pragma unroll
+  for (int q = 0; q < 11; ++q)
+    zc[q] = *reinterpret_cast<const float4 *>(&S.v1[3 * ty + q][4 + 4 * tx]);
+  const int gcol = x0 + 4 * tx;
+  const float *gxs = &S.gxs[4 + 4 * tx];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int er = 4 + 3 * ty + r;
+    const float4 xl = *reinterpret_cast<const float4 *>(&S.v1[er][4 * tx]);
+    const float4 xr = *reinterpret_cast<const float4 *>(&S.v1[er][8 + 4 * tx]);
+    const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 + 4 * tx]);
+    const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 + 4 * tx]);
+    const float gzr = SPONGE ? S.gzs[er] : 1.f;
+    res[r] = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    cen[r] = zc[r + 4];
+  }
+  if (MODE == MODE_BORN) {  // as in substep 1
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float4 cv = *reinterpret_cast<const float4 *>(&S.c[4 + 3 * ty + r][4 + 4 * tx]);
+      res[r] = born_inject4(A, b, rt.img_out_idx, z0 + 3 * ty + r - g.nb, gcol - g.CP, res[r], cv);
+    }
+  }
+}
+
 }  // namespace
 
 template <int MODE>
@@ -263,6 +352,10 @@ __global__ void __launch_bounds__(NTH, 3)
   const int smp = A.item_sample[b];
   const int shot = A.item_shot[b];
 
+  // blocks whose extended region stays clear of the sponge (g = 1 there)
+  const bool interior = (z0 - 4 >= g.nb) && (z0 + C2Z + 4 <= g.NZ - g.nb) &&
+                        (x0 - 4 >= g.X0 + g.nb) && (x0 + C2X + 4 <= g.X0 + g.NX - g.nb);
+
   // ---- 1. TMA: v^n (halo 8), d^n and c (halo 4) ----------------------------
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.bar)), "r"(1)
@@ -277,6 +370,10 @@ __global__ void __launch_bounds__(NTH, 3)
     tma_load_3d(&S.v0[0][0], &map_v, x0 - 8, z0 - 8, b, &S.bar);
     tma_load_3d(&S.d[0][0], &map_d, x0 - 4, z0 - 4, b, &S.bar);
     tma_load_3d(&S.c[0][0], &map_c, x0 - 4, z0 - 4, smp, &S.bar);
+  }
+  if (!interior) {  // the extended region's sponge factors, edge-clamped
+    if (tid < EX) S.gxs[tid] = A.gx[min(max(x0 - 4 + tid, 0), g.P - 1)];
+    if (tid < EZ) S.gzs[tid] = A.gz[min(max(z0 - 4 + tid, 0), g.NZ - 1)];
   }
   // backward imaging launches: start pulling this thread's num, den and
   // snapshot rows into L2 while the tile loads and the stencil run
@@ -310,9 +407,8 @@ __global__ void __launch_bounds__(NTH, 3)
     mbar_wait_bounded(&S.bar, 0, kWaitNs);
     return;
   }
+  if (!interior) __syncthreads();  // (block-uniform) the sponge factors are in place
 
-  const bool interior = (z0 - 4 >= g.nb) && (z0 + C2Z + 4 <= g.NZ - g.nb) &&
-                        (x0 - 4 >= g.X0 + g.nb) && (x0 + C2X + 4 <= g.X0 + g.NX - g.nb);
   const bool wide = tx < C2X / 4;  // threads that own centre columns
 
   // deferred half-precision snapshot of the INPUT field v^n (its max was
@@ -338,30 +434,11 @@ __global__ void __launch_bounds__(NTH, 3)
   }
 
   // ---- 2. substep 1 on the extended region (rows 4ty..4ty+3, cols 4tx..) --
-  {
-    float4 zc[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q)
-      zc[q] = *reinterpret_cast<const float4 *>(&S.v0[4 * ty + q][4 + 4 * tx]);
-    const int gcol = x0 - 4 + 4 * tx;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int er = 4 * ty + r;
-      const float4 xl = *reinterpret_cast<const float4 *>(&S.v0[er + 4][4 * tx]);
-      const float4 xr = *reinterpret_cast<const float4 *>(&S.v0[er + 4][8 + 4 * tx]);
-      const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 * tx]);
-      const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
-      const int grow = min(max(z0 - 4 + er, 0), g.NZ - 1);
-      const float gzr = interior ? 1.f : A.gz[grow];
-      float4 nd = update4(&zc[r], xl, xr, dv, cv, A.k, interior, gzr, A.gx, gcol, g.P);
-      if (MODE == MODE_BORN)
-        nd = born_inject4(A, b, rt.img_mid_idx, z0 - 4 + er - g.nb, gcol - g.CP, nd, cv);
-      const float4 ce = zc[r + 4];
-      *reinterpret_cast<float4 *>(&S.d[er][4 * tx]) = nd;
-      *reinterpret_cast<float4 *>(&S.v1[er][4 * tx]) =
-          make_float4(ce.x + nd.x, ce.y + nd.y, ce.z + nd.z, ce.w + nd.w);
-    }
-  }
+  // (blocks clear of the sponge run a body without the sponge formula)
+  if (interior)
+    substep1<MODE, false>(S, A, rt, b, x0, z0);
+  else
+    substep1<MODE, true>(S, A, rt, b, x0, z0);
   __syncthreads();
 
   // injection at step t1 into every cell of the extended region: add to
@@ -459,25 +536,10 @@ __global__ void __launch_bounds__(NTH, 3)
   float4 res[3];
   float4 cen[3];
   if (wide) {
-    float4 zc[11];
-#pragma unroll
-    for (int q = 0; q < 11; ++q)
-      zc[q] = *reinterpret_cast<const float4 *>(&S.v1[3 * ty + q][4 + 4 * tx]);
-    const int gcol = x0 + 4 * tx;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int er = 4 + 3 * ty + r;
-      const float4 xl = *reinterpret_cast<const float4 *>(&S.v1[er][4 * tx]);
-      const float4 xr = *reinterpret_cast<const float4 *>(&S.v1[er][8 + 4 * tx]);
-      const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 + 4 * tx]);
-      const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 + 4 * tx]);
-      const int grow = min(max(z0 + 3 * ty + r, 0), g.NZ - 1);
-      const float gzr = interior ? 1.f : A.gz[grow];
-      res[r] = update4(&zc[r], xl, xr, dv, cv, A.k, interior, gzr, A.gx, gcol, g.P);
-      if (MODE == MODE_BORN)
-        res[r] = born_inject4(A, b, rt.img_out_idx, z0 + 3 * ty + r - g.nb, gcol - g.CP, res[r], cv);
-      cen[r] = zc[r + 4];
-    }
+    if (interior)
+      substep2<MODE, false>(S, A, rt, b, x0, z0, res, cen);
+    else
+      substep2<MODE, true>(S, A, rt, b, x0, z0, res, cen);
   }
 
   // injection at step t2 on the centre (staged through the d tile)
