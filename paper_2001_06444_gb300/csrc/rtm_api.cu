@@ -307,6 +307,7 @@ static int make_map(rtm_ctx *ctx, CUtensorMap *m, const float *base, const Geo &
 struct Common {
   Geo g;
   Coef k;
+  int nsample = 1;
   DevBuf c_all, gx, gz, src_rc, rptr, rent, rext_ptr, rext_ent, rcen_ptr, rcen_ent, wav, items, err;
   CUtensorMap mc;
 };
@@ -351,6 +352,7 @@ static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_a
                         int nsample, const float *vel_d, cudaStream_t st, int step_kernel) {
   C.g = make_geo(gr);
   C.k = make_coef(gr);
+  C.nsample = nsample;
   const Geo &g = C.g;
   std::vector<double> pz, px;
   sponge_profile(g.NZ, g.nb, pz);
@@ -486,6 +488,7 @@ static void fill_args2(Step2Args &A2, const StepArgs &A, const Common &C) {
   A2.c_all = A.c_all;
   A2.item_sample = A.item_sample;
   A2.item_shot = A.item_shot;
+  A2.one_sample = C.nsample == 1;
   A2.src_row = A.src_row;
   A2.src_col = A.src_col;
   A2.wav = A.wav;

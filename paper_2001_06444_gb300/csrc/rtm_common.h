@@ -85,6 +85,7 @@ struct Step2Args {
   const float *gx, *gz;
   const float *c_all;
   const int *item_sample, *item_shot;
+  int one_sample;                // every item uses sample 0 (no lookup before the copies)
   float *v_out;                  // [B][plane] receives v^{n+2}
   float *d_out;                  // [B][plane] receives d^{n+2}
   const int *src_row, *src_col;

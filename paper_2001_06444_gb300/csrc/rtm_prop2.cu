@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(NTH, 3)
   const int b = blockIdx.z;
   const Geo &g = A.g;
   const int x0 = blockIdx.x * C2X, z0 = blockIdx.y * C2Z;
-  const int smp = A.item_sample[b];
+  const int smp = A.one_sample ? 0 : A.item_sample[b];  // c tile's sample, before the copies
   const int shot = A.item_shot[b];
 
   // blocks whose extended region stays clear of the sponge (g = 1 there)
@@ -434,10 +434,12 @@ __global__ void __launch_bounds__(NTH, 3)
   }
 
   // ---- 2. substep 1 on the extended region (rows 4ty..4ty+3, cols 4tx..) --
-  // (blocks clear of the sponge run a body without the sponge formula)
+  // (blocks clear of the sponge run a body without the sponge formula; a
+  // warp whose rows lie 4 or more past the grid skips: substep 2 reads rows
+  // up to 4 past its own, and computes none below the grid's last row + 1)
   if (interior)
     substep1<MODE, false>(S, A, rt, b, x0, z0);
-  else
+  else if (z0 - 4 + 4 * ty < g.NZ + 4)
     substep1<MODE, true>(S, A, rt, b, x0, z0);
   __syncthreads();
 
@@ -536,10 +538,14 @@ __global__ void __launch_bounds__(NTH, 3)
   float4 res[3];
   float4 cen[3];
   if (wide) {
-    if (interior)
+    if (interior) {
       substep2<MODE, false>(S, A, rt, b, x0, z0, res, cen);
-    else
+    } else if (z0 + 3 * ty < g.NZ) {
       substep2<MODE, true>(S, A, rt, b, x0, z0, res, cen);
+    } else {  // rows past the grid: nothing of them is stored
+#pragma unroll
+      for (int r = 0; r < 3; ++r) res[r] = cen[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 
   // injection at step t2 on the centre (staged through the d tile)
