@@ -22,6 +22,12 @@
 // launch from its input tile); the host pairs steps so snapshot steps land on
 // outputs.
 //
+// Most blocks lie clear of the absorbing band and run a body compiled with
+// the interior update alone.  Blocks that reach the band stage the row and
+// column sponge factors of their region in shared memory while the tiles
+// load, and evaluate the sponge form at every point (it reproduces the
+// interior update's bits where g = 1).
+//
 // Every wait is bounded: if the TMA transaction does not complete, the block
 // raises an error flag (reported as RTM_ERR_TIMEOUT) and returns.
 #include <cuda.h>

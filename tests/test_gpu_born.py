@@ -214,3 +214,35 @@ def test_least_squares_migration_against_fp64_cgls(ctx, problem):
     assert err <= 1e-3
     print(f"CGLS misfit {got[-1] / got[0]:.3e} of the start after {niter} iterations; "
           f"misfits within {max(abs(a / b - 1) for a, b in zip(got, mis)):.1e}, m within {err:.1e}")
+
+
+def test_least_squares_migration_edge_cases(ctx, problem):
+    """No iterations: the reflectivity stays zero and the one misfit is the
+    data's energy.  Zero data: the gradient vanishes at the start, so the
+    reflectivity stays zero and every misfit is zero.  Host buffers give the
+    device result bit for bit.  Checkpoint mode and a negative iteration
+    count are refused."""
+    s, vm, refl = problem
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    opts = rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0)
+    vel = torch.from_numpy(vm).cuda()
+    d = (inputs.normal(5, len(s.src_ix) * s.nt * len(s.rec_ix)) * 1e-3).astype(np.float32)
+    d = d.reshape(len(s.src_ix), s.nt, len(s.rec_ix))
+    out = torch.full((s.nz, s.nx), 7.0, dtype=torch.float32, device="cuda")
+    got = ctx.lsrtm(grid, vel, acq, torch.from_numpy(d).cuda(), opts, 0, out)
+    assert len(got) == 1 and np.isclose(got[0], float(np.vdot(d.astype(np.float64), d)), rtol=1e-6)
+    assert not out.any()
+    got = ctx.lsrtm(grid, vel, acq, torch.zeros(d.shape, dtype=torch.float32, device="cuda"),
+                    opts, 2, out)
+    assert got == [0.0, 0.0, 0.0] and not out.any()
+    dev_out = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    dev_mis = ctx.lsrtm(grid, vel, acq, torch.from_numpy(d).cuda(), opts, 1, dev_out)
+    host_out = np.zeros((s.nz, s.nx), np.float32)
+    host_mis = ctx.lsrtm(grid, vm, acq, d, opts, 1, host_out)
+    assert host_mis == dev_mis and np.array_equal(host_out, dev_out.cpu().numpy())
+    for bad_opts, niter in ((rtm.Opts(4, rtm.SNAP_F32, 1e-6, 0, 8), 1), (opts, -1)):
+        with pytest.raises(rtm.RTMError) as e:
+            ctx.lsrtm(grid, vel, acq, torch.from_numpy(d).cuda(), bad_opts, niter, out)
+        assert e.value.code == rtm.RTM_ERR_ARG
