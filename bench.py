@@ -310,6 +310,7 @@ def run_native(args, world, rank, local):
                    "batched_capacity_shots_per_s": sv["batched_capacity"]["shots_per_s"],
                    "plain_fp32_one_shot_shots_per_s": sv["plain_fp32_one_shot"]["shots_per_s"],
                    "batched_vs_plain": sv["speedup_batched_vs_plain"],
+                   "failed_requests": sv["served"]["failed"] + sv["batched_capacity"]["failed"],
                    "image_rel_l2_vs_plain_max": sv["image_rel_l2_vs_plain_max"]}
 
     if rank == 0:
@@ -373,10 +374,12 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    ctx = rtm.Context(local)
     specs = inputs.request_stream(nreq, rate_hz=1.0)
     snap = {"bf16": rtm.SNAP_BF16, "f16": rtm.SNAP_F16}[snap_name]
     reqs = [_survey_request(sp, snap, dev) for sp in specs]
+    # the context's default budget is a share of the memory free when it is
+    # created: create it after the requests' data (86 GB at 256 requests)
+    ctx = rtm.Context(local)
     for r in reqs:
         ctx.model(r["grid"], r["vt"], r["acq"], -1, r["seis"])
     torch.cuda.synchronize()
@@ -409,6 +412,7 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
                               r["opts"], r["img"].data_ptr())
             tickets.append((ctx.submit(req), sub))
         done = {}
+        errors = []
         while len(done) < len(tickets):
             for tk, sub in tickets:
                 if tk in done:
@@ -416,13 +420,17 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
                 st, _ = ctx.poll(tk, 1)
                 if st in (rtm.REQ_DONE, rtm.REQ_FAILED):
                     done[tk] = (st, time.perf_counter() - sub)
+                    if st == rtm.REQ_FAILED:
+                        errors.append(ctx.last_error())
         wall = time.perf_counter() - t0
         torch.cuda.synchronize()
         failed = sum(1 for v in done.values() if v[0] != rtm.REQ_DONE)
+        if errors:
+            print(f"serve: {failed} requests failed, first: {errors[0]}", file=sys.stderr)
         return wall, np.array([done[tk][1] for tk, _ in tickets]), failed
 
     # batched capacity: every request submitted at once
-    cap_wall, _, _ = serve(np.zeros(len(reqs)))
+    cap_wall, _, cap_failed = serve(np.zeros(len(reqs)))
     capacity = len(reqs) / cap_wall
     rate = rate_arg or 0.8 * capacity
     unit_gaps = np.diff([0.0] + [sp["t"] for sp in specs])  # unit-rate Poisson gaps
@@ -434,7 +442,8 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
     line = {
         "workload": "serve_mixed_stream", "requests": len(reqs), "shots": total_shots,
         "arrival_rate_per_s": rate, "snap_dtype": snap_name,
-        "batched_capacity": {"shots_per_s": total_shots / cap_wall, "wall_s": cap_wall},
+        "batched_capacity": {"shots_per_s": total_shots / cap_wall, "wall_s": cap_wall,
+                             "failed": cap_failed},
         "served": {"shots_per_s": total_shots / served_s, "wall_s": served_s,
                    "p50_latency_s": float(np.percentile(lat, 50)),
                    "p99_latency_s": float(np.percentile(lat, 99)), "failed": failed},

@@ -115,8 +115,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
  * device memory the context may hold for work buffers (0 = 85% of the free
- * memory at creation).  Returns RTM_ERR_ARG for a null ctx pointer or a bad
- * device, RTM_ERR_CUDA if the device cannot be initialised. */
+ * memory at creation).  Admission trusts the budget: a caller that allocates
+ * device memory of its own after creating the context should pass a budget
+ * that leaves room for it, else work admitted near the budget can fail with
+ * RTM_ERR_CUDA (out of memory).  Returns RTM_ERR_ARG for a null ctx pointer
+ * or a bad device, RTM_ERR_CUDA if the device cannot be initialised. */
 int rtm_ctx_create(rtm_ctx **ctx, int device, size_t hbm_budget_bytes);
 
 /* Destroy a context: waits (bounded) for in-flight requests, frees every
