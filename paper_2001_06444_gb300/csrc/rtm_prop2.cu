@@ -31,6 +31,8 @@
 // Every wait is bounded: if the TMA transaction does not complete, the block
 // raises an error flag (reported as RTM_ERR_TIMEOUT) and returns.
 #include <cuda.h>
+
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -701,37 +703,28 @@ int step2_ext() { return 4; }
 cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                          cudaStream_t st) {
-  static bool attr_set[4] = {false, false, false, false};
+  // the shared-memory opt-in, once per mode (launches come from several
+  // request threads; setting it twice is harmless, the flags are atomic)
+  static std::atomic<bool> attr_set[4];
   const size_t smem = step2_smem_bytes();
   dim3 grid(A.g.ntx2, A.g.ntz2, B), block(32, NTH / 32);
-  cudaError_t e = cudaSuccess;
-  if (mode == MODE_FWD) {
-    if (!attr_set[0]) {
-      e = cudaFuncSetAttribute(k_step2<MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[0] = e == cudaSuccess;
+  auto launch = [&](auto kernel, int slot) -> cudaError_t {
+    if (!attr_set[slot].load(std::memory_order_acquire)) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set[slot].store(true, std::memory_order_release);
     }
-    if (e == cudaSuccess) k_step2<MODE_FWD><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
-  } else if (mode == MODE_MODEL) {
-    if (!attr_set[1]) {
-      e = cudaFuncSetAttribute(k_step2<MODE_MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[1] = e == cudaSuccess;
-    }
-    if (e == cudaSuccess) k_step2<MODE_MODEL><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
-  } else if (mode == MODE_BORN) {
-    if (!attr_set[3]) {
-      e = cudaFuncSetAttribute(k_step2<MODE_BORN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[3] = e == cudaSuccess;
-    }
-    if (e == cudaSuccess) k_step2<MODE_BORN><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
-  } else {
-    if (!attr_set[2]) {
-      e = cudaFuncSetAttribute(k_step2<MODE_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_set[2] = e == cudaSuccess;
-    }
-    if (e == cudaSuccess) k_step2<MODE_BWD><<<grid, block, smem, st>>>(mv, md, mc, A, rt);
+    kernel<<<grid, block, smem, st>>>(mv, md, mc, A, rt);
+    return cudaGetLastError();
+  };
+  switch (mode) {
+    case MODE_FWD: return launch(k_step2<MODE_FWD>, 0);
+    case MODE_MODEL: return launch(k_step2<MODE_MODEL>, 1);
+    case MODE_BWD: return launch(k_step2<MODE_BWD>, 2);
+    case MODE_BORN: return launch(k_step2<MODE_BORN>, 3);
   }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace rtm
