@@ -318,7 +318,12 @@ int oracle_migrate(const or_grid *gr, const double *vel, int nshot,
     }
     double dmax = 0.0;
     for (size_t q = 0; q < npix; ++q) dmax = den[q] > dmax ? den[q] : dmax;
-    for (size_t q = 0; q < npix; ++q) stack[q] += num[q] / (den[q] + eps * dmax);
+    /* a pixel with a zero denominator (never reached by the source
+       wavefield, or no imaging step at all) contributes 0 */
+    for (size_t q = 0; q < npix; ++q) {
+      const double dd = den[q] + eps * dmax;
+      stack[q] += dd > 0.0 ? num[q] / dd : 0.0;
+    }
     if (num_out) memcpy(num_out + (size_t)s * npix, num, npix * sizeof(double));
     if (den_out) memcpy(den_out + (size_t)s * npix, den, npix * sizeof(double));
   }

@@ -136,3 +136,27 @@ def test_flat_reflector_depth_and_sign():
     k = iz0 + int(np.argmax(np.abs(prof_zp[iz0:iz1])))
     assert abs(k * s.dz - 495.0) <= 10.0, k
     assert prof_zp[k] > 0
+
+
+def test_zero_denominator_contributes_zero():
+    """Eq. 5 with the stabiliser, at pixels whose denominator is zero: with
+    no imaging step (isnap > nt) every pixel has den = 0 and the image is
+    exactly zero, not 0/0; with eps = 0 the pixels the source wavefield has
+    not reached contribute zero and the rest are finite."""
+    nx, nz, nt = 30, 20, 60
+    v = np.full((nz, nx), 2000.0)
+    g = oracle.grid(nx, nz, 8, 10.0, 10.0, 1e-3, nt)
+    w = inputs.ricker(20.0, 1e-3, nt)
+    rix, riz = np.arange(nx, dtype=np.int32), np.zeros(nx, np.int32)
+    sx, sz = np.array([15], np.int32), np.array([3], np.int32)
+    d = oracle.model(g, v, 15, 3, rix, riz, w)[None]
+    img = oracle.migrate(g, v, sx, sz, rix, riz, w, d, isnap=64)
+    assert np.all(img == 0.0)
+    # 3 steps: the stencil reaches 12 cells from the source, so the far
+    # pixels' denominators are exactly zero
+    g3 = oracle.grid(nx, nz, 8, 10.0, 10.0, 1e-3, 3)
+    d3 = oracle.model(g3, v, 15, 3, rix, np.full(nx, 3, np.int32), w[:3])[None]
+    img, num, den = oracle.migrate(g3, v, sx, sz, rix, np.full(nx, 3, np.int32), w[:3], d3,
+                                   isnap=1, eps=0.0, laplacian=False, return_parts=True)
+    assert np.all(np.isfinite(img)) and np.any(den[0] == 0.0)
+    assert np.all(img[den[0] == 0.0] == 0.0) and np.any(img != 0.0)
