@@ -403,3 +403,57 @@ def test_velocity_ensemble_uncertainty_maps(ctx):
     # the water layer is not perturbed: zero std, confidence 1 there
     assert np.all(out[1].cpu().numpy().reshape(s.nz, s.nx)[:40] == 0.0)
     assert np.all(c.cpu().numpy().reshape(s.nz, s.nx)[:40] == 1.0)
+
+
+def _small(nx, nz, nb, nt, sx, sz, rec_iz):
+    v = np.full((nz, nx), 2000.0, np.float32)
+    s = inputs.Survey(nx, nz, nb, 10.0, 10.0, 1e-3, nt, v, np.array([sx], np.int32),
+                      np.array([sz], np.int32), np.arange(nx, dtype=np.int32),
+                      np.full(nx, rec_iz, np.int32), inputs.ricker(20.0, 1e-3, nt))
+    return s, v
+
+
+@pytest.mark.parametrize("case", ["no_imaging_step", "one_step", "one_cell", "no_sponge"])
+def test_degenerate_migrations(ctx, case):
+    """Degenerate cases against the oracle: no imaging step (isnap > nt: the
+    image is exactly zero, reading 7's zero denominator), a single time step
+    (receivers on the source row), a 1 x 1 grid (its filtered image is zero,
+    so the raw image is compared too), and no sponge (nb = 0)."""
+    if case == "no_imaging_step":
+        s, v = _small(30, 20, 8, 50, 15, 3, 0)
+        data = ora_model(s, v)[None]
+        got = gpu_migrate(ctx, s, v, data, isnap=64)
+        assert np.all(got == 0.0) and np.all(ora_migrate(s, v, data, isnap=64) == 0.0)
+        return
+    s, v, isnap = {"one_step": _small(30, 20, 8, 1, 15, 3, 3) + (1,),
+                   "one_cell": _small(1, 1, 3, 40, 0, 0, 0) + (2,),
+                   "no_sponge": _small(40, 24, 0, 120, 20, 2, 0) + (3,)}[case]
+    want = ora_model(s, v)
+    got = gpu_model(ctx, s, v)
+    assert np.abs(want).max() > 0 and rel_l2(got, want) <= SEIS_TOL
+    data = f32(want)[None]
+    for lap in (True, False):
+        gi, oi = gpu_migrate(ctx, s, v, data, isnap=isnap, lap=lap), ora_migrate(s, v, data, isnap,
+                                                                                 lap=lap)
+        if not np.any(oi):
+            assert case == "one_cell" and lap and np.all(gi == 0.0)
+        else:
+            assert rel_l2(gi, oi) <= IMG_TOL, (case, lap)
+
+
+def test_empty_acquisitions_are_refused(ctx):
+    s, v = _small(30, 20, 8, 50, 15, 3, 0)
+    keep = rtm._Keep()
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    seis = torch.zeros((1, s.nt, s.nx), dtype=torch.float32, device="cuda")
+    opts = rtm.Opts(1, rtm.SNAP_F32, 1e-6, 1)
+    none = np.zeros(0, np.int32)
+    for acq, grid in ((rtm.make_acq(keep, none, none, s.rec_ix, s.rec_iz, f32(s.wavelet)),
+                       rtm.make_grid(*s.grid_tuple())),
+                      (rtm.make_acq(keep, s.src_ix, s.src_iz, none, none, f32(s.wavelet)),
+                       rtm.make_grid(*s.grid_tuple())),
+                      (rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet)),
+                       rtm.make_grid(s.nx, s.nz, s.nb, s.dx, s.dz, s.dt, 0))):
+        with pytest.raises(rtm.RTMError) as e:
+            ctx.migrate(grid, dev(v), acq, seis, opts, img)
+        assert e.value.code == rtm.RTM_ERR_ARG
