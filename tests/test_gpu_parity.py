@@ -457,3 +457,33 @@ def test_empty_acquisitions_are_refused(ctx):
         with pytest.raises(rtm.RTMError) as e:
             ctx.migrate(grid, dev(v), acq, seis, opts, img)
         assert e.value.code == rtm.RTM_ERR_ARG
+
+
+def test_size_limits(ctx):
+    """The statistics kernel at its largest sample count (32768: one pixel per
+    block, a 128 KB sort in shared memory) against the oracle, one sample
+    more refused; a grid beyond the 2^31-point padded limit refused before
+    any array is read."""
+    n, npix = 32768, 37
+    x = f32(inputs.normal(3, n * npix).reshape(n, npix))
+    out = [torch.zeros(npix, dtype=t, device="cuda")
+           for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+    ctx.ensemble_stats(torch.from_numpy(x).cuda(), *out)
+    torch.cuda.synchronize()
+    m, sd, a, b = oracle.ensemble_stats(x)
+    assert np.allclose(out[0].cpu().numpy(), m, rtol=1e-12, atol=1e-13)
+    assert np.allclose(out[1].cpu().numpy(), sd, rtol=1e-12, atol=1e-13)
+    assert np.array_equal(out[2].cpu().numpy(), a.astype(np.float32))
+    assert np.array_equal(out[3].cpu().numpy(), b.astype(np.float32))
+    with pytest.raises(rtm.RTMError) as e:
+        ctx.ensemble_stats(torch.zeros((n + 1, npix), dtype=torch.float32, device="cuda"), *out)
+    assert e.value.code == rtm.RTM_ERR_ARG
+    s, v = _small(30, 20, 8, 50, 15, 3, 0)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+    huge = rtm.make_grid(50000, 50000, 20, 10.0, 10.0, 1e-3, 50)
+    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+    with pytest.raises(rtm.RTMError) as e:
+        ctx.migrate(huge, dev(v), acq, torch.zeros((1, 50, 30), device="cuda"),
+                    rtm.Opts(1, rtm.SNAP_F32, 1e-6, 1), img)
+    assert e.value.code == rtm.RTM_ERR_ARG
