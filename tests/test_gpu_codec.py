@@ -136,3 +136,49 @@ def test_nonfinite_and_malformed_are_reported(ctx):
     ctx.decompress(good, stride, 2, 40, 40, y)  # the context is still usable
     assert np.array_equal(y.cpu().numpy()[1], oracle.codec_decompress(
         oracle.codec_compress(x[2], 1e-3), 40, 40))
+
+
+def test_migration_through_the_codec(ctx):
+    """The paper's compression-error experiment (§4.2) on the flat-reflector
+    survey: seismograms and velocity passed through the codec, then migrated.
+    Lossless round trips give the uncompressed image bit for bit.  At 1e-4
+    the image is linear in the data (the illumination denominator depends on
+    the velocity alone), so its relative error stays within a small multiple
+    of the seismograms' relative error."""
+    import oracle
+    from conftest import rel_l2
+
+    s = inputs.flat_reflector(nt=600)
+    g = oracle.grid(*s.grid_tuple())
+    w = s.wavelet.astype(np.float32).astype(np.float64)
+    seis = np.stack([oracle.model(g, s.vel.astype(np.float64), s.src_ix[k], s.src_iz[k],
+                                  s.rec_ix, s.rec_iz, w) for k in range(len(s.src_ix))])
+    seis = torch.from_numpy(seis.astype(np.float32)).cuda()
+    vel = torch.from_numpy(s.vel.astype(np.float32)).cuda()[None].contiguous()
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*s.grid_tuple())
+    opts = rtm.Opts(2, rtm.SNAP_F32, 1e-6, 1)
+
+    def migrate(sd, vd):
+        img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+        ctx.migrate(grid, vd[0], acq, sd, opts, img)
+        torch.cuda.synchronize()
+        return img.cpu().numpy()
+
+    def round_trip(x, tol):
+        count, n0, n1 = x.shape
+        stride = (rtm.compress_bound(n0, n1) + 15) // 16 * 16
+        out = torch.empty(count * stride, dtype=torch.uint8, device="cuda")
+        back = torch.empty_like(x)
+        ctx.compress(x, tol, out, stride)
+        ctx.decompress(out, stride, count, n0, n1, back)
+        return back
+
+    ref = migrate(seis, vel)
+    assert np.array_equal(migrate(round_trip(seis, 0.0), round_trip(vel, 0.0)), ref)
+    sq = round_trip(seis, 1e-4)
+    data_err = rel_l2(sq.cpu().numpy(), seis.cpu().numpy())
+    img_err = rel_l2(migrate(sq, round_trip(vel, 1e-4)), ref)
+    assert 0 < data_err and img_err <= 10 * data_err, (img_err, data_err)
+    print(f"1e-4: seismograms within {data_err:.1e}, image within {img_err:.1e} (relative L2)")
