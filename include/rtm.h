@@ -158,6 +158,7 @@ typedef struct {
   long long eik_launches;
   double eik_ms;
   double eik_updates;
+  long long graph_launches;  /* phases replayed as one captured CUDA graph (counted always) */
 } rtm_stats;
 
 /* Turn profiling on (1) or off (0).  With profiling on, every migration

@@ -561,6 +561,10 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
   const cudaError_t el = cudaGraphLaunch(ex, st);
   cudaGraphExecDestroy(ex);  // released once the launch completes
   if (el != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(el));
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stats.graph_launches += 1;
+  }
   return RTM_OK;
 }
 

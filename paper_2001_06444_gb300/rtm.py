@@ -65,7 +65,8 @@ class Stats(C.Structure):
                 ("launches", C.c_longlong), ("migrations", C.c_longlong),
                 ("codec_launches", C.c_longlong), ("codec_ms", C.c_double),
                 ("codec_bytes", C.c_double), ("eik_launches", C.c_longlong),
-                ("eik_ms", C.c_double), ("eik_updates", C.c_double)]
+                ("eik_ms", C.c_double), ("eik_updates", C.c_double),
+                ("graph_launches", C.c_longlong)]
 
 
 class Request(C.Structure):

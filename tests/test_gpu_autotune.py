@@ -22,12 +22,15 @@ def _problem():
     return s, v, seis
 
 
-def _migrate(ctx, s, v, seis, opts):
+def _migrate(ctx, s, v, seis, opts, stream=None):
+    """Migrate on `stream` (None: the legacy default stream, where the
+    library launches directly; a created stream lets it capture graphs)."""
     keep = rtm._Keep()
     acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
-    img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
-    ctx.migrate(rtm.make_grid(*s.grid_tuple()), torch.from_numpy(v).cuda(), acq,
-                torch.from_numpy(seis).cuda(), opts, img)
+    with torch.cuda.stream(stream or torch.cuda.default_stream()):
+        img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+        ctx.migrate(rtm.make_grid(*s.grid_tuple()), torch.from_numpy(v).cuda(), acq,
+                    torch.from_numpy(seis).cuda(), opts, img)
     torch.cuda.synchronize()
     return img.cpu().numpy()
 
@@ -38,12 +41,14 @@ def test_autotune_and_graph_capture_are_bitwise_neutral(dtype):
     opts = rtm.Opts(4, dtype, 1e-6, 1)
     keep = rtm._Keep()
     acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, s.wavelet.astype(np.float32))
+    side = torch.cuda.Stream()
     with rtm.Context(0) as ctx:
         base = _migrate(ctx, s, v, seis, opts)
         choice = ctx.autotune(rtm.make_grid(*s.grid_tuple()), acq, opts, trial_steps=40)
         assert choice["step_kernel"] in (1, 2) and choice["graph"] in (0, 1)
         assert choice["max_items"] >= 0
         assert np.array_equal(_migrate(ctx, s, v, seis, opts), base)
+        assert np.array_equal(_migrate(ctx, s, v, seis, opts, side), base)
     old = os.environ.get("RTM_GRAPHS")
     os.environ["RTM_GRAPHS"] = "1"
     try:
@@ -54,7 +59,11 @@ def test_autotune_and_graph_capture_are_bitwise_neutral(dtype):
         else:
             os.environ["RTM_GRAPHS"] = old
     try:
-        g.set_batch(2)  # two batches, each phase replayed from a graph
-        assert np.array_equal(_migrate(g, s, v, seis, opts), base)
+        g.set_batch(2)  # two batches, each phase captured and replayed as a graph
+        g.set_profiling(True)
+        g.stats(reset=True)
+        assert np.array_equal(_migrate(g, s, v, seis, opts, side), base)
+        st = g.stats(reset=True)
+        assert st["graph_launches"] >= 4, st  # 2 batches x (forward, backward)
     finally:
         g.close()
