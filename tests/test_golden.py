@@ -39,3 +39,16 @@ def test_every_table_entry_is_present_and_ordered():
         # a looser tolerance never gives a larger file
         assert t[(arr, 1e-1)][0] <= t[(arr, 1e-4)][0] <= t[(arr, 0.0)][0] < 1.0
     assert max(t[("seismogram", 1e-4)]) < min(t[("seismogram", 0.0)]) < 1.0
+
+
+def test_bench_reads_the_fixture():
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
+
+    t = bench.paper_compression_tables()
+    assert t[("seismogram", 1e-4)] == (8.38 / 76.20, 13.38 / 76.20)
+    assert t[("velocity", 1e-1)] == 2.98 / 6.10 and t[("image", 0.0)] == 5.34 / 6.10
