@@ -621,13 +621,18 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   const double bwd_bytes = gr.nt * 16.0 * upd +
                            nsnap * ((double)esz + (born_refl ? 4.0 : 16.0)) * pix;
   long long launches = 0, step_launches = 0;
-  std::vector<cudaEvent_t> ev;
+  struct Events {  // phase-timing events (profiling), destroyed on every path
+    std::vector<cudaEvent_t> v;
+    ~Events() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } ev;
   auto mark = [&]() -> int {
     if (!ctx->prof) return RTM_OK;
     cudaEvent_t e;
     CU(cudaEventCreate(&e));
+    ev.v.push_back(e);
     CU(cudaEventRecord(e, st));
-    ev.push_back(e);
     return RTM_OK;
   };
 
@@ -859,12 +864,11 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   double ms_total = 0.0;
   if (ctx->prof) {
     CU(cudaStreamSynchronize(st));
-    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+    for (size_t i = 0; i + 1 < ev.v.size(); i += 2) {
       float ms = 0.f;
-      CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      CU(cudaEventElapsedTime(&ms, ev.v[i], ev.v[i + 1]));
       ms_total += ms;
     }
-    for (auto e : ev) cudaEventDestroy(e);
   }
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1163,9 +1167,18 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
       rc = fail(ctx, RTM_ERR_CUDA, "trial inputs");
       break;
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    struct Pair {  // trial timing events, released on every path
+      cudaEvent_t a = nullptr, b = nullptr;
+      ~Pair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } ev2;
+    if (cudaEventCreate(&ev2.a) != cudaSuccess || cudaEventCreate(&ev2.b) != cudaSuccess) {
+      rc = fail(ctx, RTM_ERR_CUDA, "trial events");
+      break;
+    }
+    const cudaEvent_t e0 = ev2.a, e1 = ev2.b;
     for (size_t i = 0; i < cand.size() && !rc; ++i) {
       const RunConfig &c = cand[i];
       const long long cap = c.max_items > 0 ? c.max_items : bmax;
@@ -1186,8 +1199,6 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
         best = (int)i;
       }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
   } while (0);
   vel.release();
   seis.release();

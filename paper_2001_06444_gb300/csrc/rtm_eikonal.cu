@@ -344,12 +344,16 @@ extern "C" int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, i
     df = dfields.as<float>();
   }
   EIK_CU(diters.alloc(ctx, (size_t)problems * 4, st));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ctx->prof) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
-  }
+  struct Timer {  // the solver's device time (profiling), released on every path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Timer() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } tm;
+  if (ctx->prof && cudaEventCreate(&tm.a) == cudaSuccess && cudaEventCreate(&tm.b) == cudaSuccess)
+    cudaEventRecord(tm.a, st);
+  const cudaEvent_t e0 = tm.b ? tm.a : nullptr, e1 = tm.b;
   EIK_CU(launch_eikonal(dslow.as<float>(), nsample, nz, nx, dz, dx, nsrc, dtab.as<int>(), nrec,
                         dtab.as<int>() + 2 * nsrc, max_iter, dt, df, diters.as<int>(), resident,
                         st));
@@ -374,10 +378,6 @@ extern "C" int rtm_eikonal(rtm_ctx *ctx, int nz, int nx, double dz, double dx, i
       ctx->stats.eik_ms += ms;
       ctx->stats.eik_updates += 4.0 * (double)sweeps * (double)N;
     }
-  }
-  if (e0) {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
   }
   if (iters) std::copy(it.begin(), it.end(), iters);
   if (stuck)
