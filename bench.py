@@ -33,6 +33,11 @@ from paper_2001_06444_gb300.sharding import barrier, max_over_ranks  # noqa: E40
 
 METRIC = "RTM shots/s & Gpt-updates/s vs HBM roofline; p50/p99 latency, mixed stream"
 WORKLOAD = "rtm_1701x351_96shots_nt5000_isnap4_f32snap"
+STEP_KERNEL_NAMES = {
+    3: "k_step2p (persistent two-step TMA kernel, two-stage copy ring; forward+backward phases)",
+    2: "k_step2 (two-step TMA kernel, one tile per block; forward+backward phases)",
+    1: "k_step (single-step kernel; forward+backward phases)",
+}
 
 
 def parse():
@@ -42,6 +47,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--batch", type=int, default=0, help="items in flight (0 = memory budget)")
+    # a fixed launch configuration instead of the autotuner's choice (for
+    # comparisons and profiler captures of one kernel)
+    p.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                   help="0 autotune; 1 single-step; 2 two-step, one tile per block; "
+                        "3 persistent two-step")
+    p.add_argument("--tile-z", type=int, default=24, choices=[16, 24],
+                   help="with --kernel 3: centre rows of a tile")
+    p.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                   help="with --kernel 1-3: capture each phase in a CUDA graph")
     p.add_argument("--snap", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--checkpoint", type=int, default=0,
                    help="0 keep every snapshot; C>0 / -1 recompute from checkpoints")
@@ -90,7 +104,7 @@ def profile_traffic():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("rtm_prop.cu", "rtm_prop2.cu"):
+    for f in ("rtm_prop.cu", "rtm_prop2.cu", "rtm_prop2p.cu", "rtm_step2_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2001_06444_gb300", "csrc", f), "rb").read())
     digest = h.hexdigest()[:16]
     summ = os.path.join(ROOT, "profiles", "k_step2_small.md")
@@ -218,12 +232,21 @@ def run_native(args, world, rank, local):
     vel_mig = torch.from_numpy(vm.astype(np.float32)).to(dev)
     seis = torch.empty((s.nshot, s.nt, s.nrec), dtype=torch.float32, device=dev)
     image = torch.empty((s.nz, s.nx), dtype=torch.float32, device=dev)
+    if args.kernel:
+        # the context's default launch configuration, read when it is created
+        os.environ["RTM_STEP_KERNEL"] = str(args.kernel)
+        os.environ["RTM_TILE_Z"] = str(args.tile_z)
+        os.environ["RTM_GRAPHS"] = str(args.graphs)
     ctx = rtm.Context(local)
     ctx.model(grid, vel_true, acq, -1, seis)  # observed data, untimed
     torch.cuda.synchronize()
     if args.batch:
         ctx.set_batch(args.batch)
-    tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
+    if args.kernel:
+        tuned = {"step_kernel": args.kernel, "max_items": args.batch, "graph": args.graphs,
+                 "tile_z": args.tile_z if args.kernel == 3 else 24, "fixed": True}
+    else:
+        tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
     for _ in range(args.warmup):
         ctx.migrate(grid, vel_mig, acq, seis, opts, image)
     torch.cuda.synchronize()
@@ -311,6 +334,7 @@ def run_native(args, world, rank, local):
                    "arrival_rate_per_s": sv["arrival_rate_per_s"],
                    "served_shots_per_s": sv["served"]["shots_per_s"],
                    "batched_capacity_shots_per_s": sv["batched_capacity"]["shots_per_s"],
+                   "batched_capacity_gpt_updates_per_s": sv["batched_capacity"]["gpt_updates_per_s"],
                    "plain_fp32_one_shot_shots_per_s": sv["plain_fp32_one_shot"]["shots_per_s"],
                    "batched_vs_plain": sv["speedup_batched_vs_plain"],
                    "failed_requests": sv["served"]["failed"] + sv["batched_capacity"]["failed"],
@@ -335,7 +359,7 @@ def run_native(args, world, rank, local):
             "gpt_updates_per_s": gpt,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "kernel": "k_step2 (two-step TMA kernel; forward+backward phases)",
+                         "kernel": STEP_KERNEL_NAMES.get(tuned.get("step_kernel"), "k_step"),
                          "peak_kind": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes_per_launch": stats["step_bytes"] / max(1, launches_step),
                          "avg_launch_us": 1e3 * stats["step_ms"] / max(1, launches_step)},
@@ -389,6 +413,9 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
         ctx.model(r["grid"], r["vt"], r["acq"], -1, r["seis"])
     torch.cuda.synchronize()
     total_shots = sum(r["s"].nshot for r in reqs)
+    # padded point updates of the whole stream (forward + backward)
+    total_upd = sum(2.0 * r["s"].nshot * r["s"].nt * (r["s"].nz + 2 * r["s"].nb) *
+                    (r["s"].nx + 2 * r["s"].nb) for r in reqs)
     # plain form: one request at a time, one shot in flight, FP32 snapshots
     ctx.set_batch(1)
     t = time.perf_counter()
@@ -448,11 +475,13 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
         "workload": "serve_mixed_stream", "requests": len(reqs), "shots": total_shots,
         "arrival_rate_per_s": rate, "snap_dtype": snap_name,
         "batched_capacity": {"shots_per_s": total_shots / cap_wall, "wall_s": cap_wall,
+                             "gpt_updates_per_s": total_upd / cap_wall / 1e9,
                              "failed": cap_failed},
         "served": {"shots_per_s": total_shots / served_s, "wall_s": served_s,
                    "p50_latency_s": float(np.percentile(lat, 50)),
                    "p99_latency_s": float(np.percentile(lat, 99)), "failed": failed},
-        "plain_fp32_one_shot": {"shots_per_s": total_shots / plain_s, "wall_s": plain_s},
+        "plain_fp32_one_shot": {"shots_per_s": total_shots / plain_s, "wall_s": plain_s,
+                                "gpt_updates_per_s": total_upd / plain_s / 1e9},
         "speedup_batched_vs_plain": plain_s / cap_wall,
         "image_rel_l2_vs_plain_max": max(errs),
         "grids": sorted({(sp["nx"], sp["nz"]) for sp in specs}),

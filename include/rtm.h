@@ -62,7 +62,7 @@ typedef enum {
   RTM_ERR_ARG = 1,     /* bad shape, null pointer, index outside the physical grid */
   RTM_ERR_CFL = 2,     /* the velocity violates the leapfrog stability bound       */
   RTM_ERR_NOMEM = 3,   /* the work can never fit the context's memory budget       */
-  RTM_ERR_BUSY = 4,    /* request queue full                                        */
+  RTM_ERR_BUSY = 4,    /* request queue full; context still running requests        */
   RTM_ERR_TIMEOUT = 5, /* a bounded wait expired                                    */
   RTM_ERR_CUDA = 6,    /* a CUDA runtime call failed                                */
   RTM_ERR_STATE = 7    /* unknown ticket or context state                           */
@@ -122,8 +122,10 @@ typedef struct {
  * or a bad device, RTM_ERR_CUDA if the device cannot be initialised. */
 int rtm_ctx_create(rtm_ctx **ctx, int device, size_t hbm_budget_bytes);
 
-/* Destroy a context: waits (bounded) for in-flight requests, frees every
- * buffer it owns.  NULL is accepted. */
+/* Destroy a context: cancels queued requests, waits (bounded, 600 s) for
+ * running ones, frees every buffer it owns.  If requests are still running
+ * after the bound, returns RTM_ERR_BUSY and leaves the context alive (the
+ * call may be repeated).  NULL is accepted. */
 int rtm_ctx_destroy(rtm_ctx *ctx);
 
 /* Cap the number of (sample, shot) migrations the context keeps in flight at
@@ -159,6 +161,8 @@ typedef struct {
   double eik_ms;
   double eik_updates;
   long long graph_launches;  /* phases replayed as one captured CUDA graph (counted always) */
+  long long requests_peak_running;  /* most request-loop requests running at once */
+  long long requests_backfilled;    /* requests started past an older one waiting for memory */
 } rtm_stats;
 
 /* Turn profiling on (1) or off (0).  With profiling on, every migration
@@ -170,15 +174,19 @@ int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset);
 
 /* Choose how migrations shaped like (grid, acq, opts) are launched on this
  * context, by timing short trial migrations (trial_steps time steps, 64 if
- * <= 0) of every candidate on synthetic inputs: time-block depth (the
- * two-step kernel, which advances each grid two steps per launch with a
- * 120 x 24 tile plus a 4-point ring, or the single-step kernel), the number
- * of migrations in flight, and whether each phase of a batch is captured
- * and replayed as a CUDA graph.  The fastest is used by later rtm_migrate,
- * rtm_migrate_ensemble and request-loop calls with the same grid, nt, isnap
- * and snapshot format.  All candidates give bit-identical results.
- * choice (nullable, 3 ints): {step kernel 1 or 2, items cap (0 = memory),
- * graph 0 or 1}.  Synchronises the stream. */
+ * <= 0) of every candidate on synthetic inputs:
+ *   - the propagation kernel and its tile: the persistent two-step kernel
+ *     (kernel 3: two blocks per SM walk the tile list, the copies of the next
+ *     tile overlapping the current one) with 120 x 24 or 120 x 16 centre
+ *     tiles, the two-step kernel with one 120 x 24 tile per block (kernel 2),
+ *     or the single-step kernel (kernel 1);
+ *   - the number of migrations in flight;
+ *   - whether each phase of a batch is captured and replayed as a CUDA graph.
+ * The fastest is used by later rtm_migrate, rtm_migrate_ensemble and
+ * request-loop calls with the same grid, nt, isnap and snapshot format.  All
+ * candidates give bit-identical results.
+ * choice (nullable, 4 ints): {kernel 1, 2 or 3, items cap (0 = memory),
+ * graph 0 or 1, tile height 24 or 16}.  Synchronises the stream. */
 int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq,
                  const rtm_opts *opts, int trial_steps, int *choice, void *stream);
 
@@ -289,6 +297,10 @@ typedef struct {
 
 /* Queue a migration request; its shots join the device work of requests
  * already in flight as soon as memory for their snapshot buffers is free.
+ * Requests start in arrival order, except that while the oldest waits for
+ * memory a later one that fits in what is free may start first (at most 16
+ * times per waiting request).  A request whose device-side wait gave up ends
+ * FAILED with RTM_ERR_TIMEOUT; other requests are not affected.
  * Returns RTM_ERR_NOMEM if the request could never fit the budget,
  * RTM_ERR_BUSY if the queue is full, RTM_ERR_CFL / RTM_ERR_ARG as rtm_migrate. */
 int rtm_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket);
@@ -325,6 +337,18 @@ int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const rtm_acq *acq
  * milliseconds, and stores in *raised 1 if the flag came back to the host.
  * Synchronises the stream. */
 int rtm_selftest_wait(rtm_ctx *ctx, int wait_ms, int *raised, void *stream);
+
+/* Test hook for the reporting of device-side failures (no counterpart in the
+ * paper).  The next `count` migration or modelling calls on this context
+ * (direct calls, request-loop requests or autotuner trials, in the order they
+ * start) run normally but begin with their wait-timeout flag already raised,
+ * exactly as if one of their bounded device-side waits had given up.  So the
+ * path that reports it can be tested without making a GPU wait run out: a
+ * call that synchronises returns RTM_ERR_TIMEOUT itself, an asynchronous
+ * call's flag is returned by the next call on the context, a request ends
+ * FAILED with RTM_ERR_TIMEOUT, and no other call or request is affected.
+ * count = 0 cancels what is left; RTM_ERR_ARG for count < 0. */
+int rtm_ctx_inject_wait_timeout(rtm_ctx *ctx, int count);
 
 /* ------------------------------------------------------------- codec --
  * Error-bounded compression of velocity models, images and seismograms

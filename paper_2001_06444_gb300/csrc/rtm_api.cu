@@ -30,15 +30,116 @@
 
 namespace rtm {
 
+static thread_local char t_err[512] = "no error";
+
 int fail(rtm_ctx *ctx, int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof(t_err), fmt, ap);
+  va_end(ap);
   if (ctx) {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
-    va_end(ap);
+    std::memcpy(ctx->err, t_err, sizeof(ctx->err));
   }
   return code;
+}
+
+const char *thread_error() { return t_err; }
+
+// ------------------------------------------------ wait-timeout flag slots --
+
+// Reap pending slots whose copies have landed (with `wait_oldest`, wait for
+// the oldest first); a raised one sets timeout_seen.  flag_mu held.
+static void reap_flags(rtm_ctx *ctx, bool wait_oldest) {
+  for (auto it = ctx->pending.begin(); it != ctx->pending.end();) {
+    const bool first = it == ctx->pending.begin();
+    const cudaError_t q =
+        (wait_oldest && first) ? cudaEventSynchronize(it->ev) : cudaEventQuery(it->ev);
+    if (q == cudaErrorNotReady) {
+      ++it;
+      continue;
+    }
+    if (q != cudaSuccess) cudaGetLastError();
+    const volatile int *f = ctx->h_flags + 2 * it->slot;
+    if (f[0] && !ctx->seen_code) {
+      ctx->seen_code = f[0];
+      ctx->seen_line = f[1];
+    }
+    cudaEventDestroy(it->ev);
+    ctx->free_flags.push_back(it->slot);
+    it = ctx->pending.erase(it);
+  }
+}
+
+int flag_acquire(rtm_ctx *ctx) {
+  std::lock_guard<std::mutex> lk(ctx->flag_mu);
+  if (ctx->free_flags.empty()) reap_flags(ctx, false);
+  while (ctx->free_flags.empty() && !ctx->pending.empty()) reap_flags(ctx, true);
+  if (ctx->free_flags.empty()) return -1;  // more calls in flight than slots
+  const int s = ctx->free_flags.back();
+  ctx->free_flags.pop_back();
+  volatile int *f = ctx->h_flags + 2 * s;
+  f[0] = f[1] = 0;
+  return s;
+}
+
+int flag_take(rtm_ctx *ctx, int slot, int *line) {
+  *line = 0;
+  if (slot < 0) return 0;
+  std::lock_guard<std::mutex> lk(ctx->flag_mu);
+  const volatile int *f = ctx->h_flags + 2 * slot;
+  const int code = f[0];
+  *line = f[1];
+  ctx->free_flags.push_back(slot);
+  return code;
+}
+
+int flag_status(rtm_ctx *ctx, int code, int line, const char *whose) {
+  if (!code) return RTM_OK;
+  if (code == 2)
+    return fail(ctx, RTM_ERR_STATE,
+                "a device index check failed in %s (kernel source line %d, debug build); the "
+                "access was skipped",
+                whose, line);
+  return fail(ctx, RTM_ERR_TIMEOUT, "a device-side wait gave up in %s", whose);
+}
+
+void flag_defer(rtm_ctx *ctx, int slot, cudaStream_t st) {
+  if (slot < 0) return;
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(ev, st) != cudaSuccess) {
+    // no event: wait for the stream here so the slot can be read now
+    cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lk(ctx->flag_mu);
+    const volatile int *f = ctx->h_flags + 2 * slot;
+    if (f[0] && !ctx->seen_code) {
+      ctx->seen_code = f[0];
+      ctx->seen_line = f[1];
+    }
+    ctx->free_flags.push_back(slot);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(ctx->flag_mu);
+  ctx->pending.push_back(rtm_ctx::PendingFlag{slot, ev});
+}
+
+// A kernel whose bounded wait gave up raises its call's flag; a call that
+// synchronises reports it itself, an asynchronous call's flag is reported by
+// the first call on the context that finds it complete.
+int check_wait_flag(rtm_ctx *ctx) {
+  int code, line;
+  {
+    std::lock_guard<std::mutex> lk(ctx->flag_mu);
+    reap_flags(ctx, false);
+    code = ctx->seen_code;
+    line = ctx->seen_line;
+    ctx->seen_code = ctx->seen_line = 0;
+  }
+  return flag_status(ctx, code, line, "an earlier call");
 }
 
 #define CU(call)                                                                         \
@@ -73,7 +174,7 @@ bool is_device_ptr(const void *p) {
 
 static long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
 
-Geo make_geo(const rtm_grid &gr) {
+Geo make_geo(const rtm_grid &gr, int tile_z) {
   Geo g;
   g.nb = gr.nb;
   g.nz = gr.nz;
@@ -88,7 +189,8 @@ Geo make_geo(const rtm_grid &gr) {
   g.ntx = (g.P + TX - 1) / TX;
   g.ntz = (g.NZ + TZ - 1) / TZ;
   g.ntx2 = (g.P + step2_tile_x() - 1) / step2_tile_x();
-  g.ntz2 = (g.NZ + step2_tile_z() - 1) / step2_tile_z();
+  g.tz2 = tile_z;
+  g.ntz2 = (g.NZ + tile_z - 1) / tile_z;
   g.plane = (long long)g.NZ * g.P;
   g.pplane = (long long)g.nz * g.SX;
   return g;
@@ -129,7 +231,7 @@ int checkpoint_steps(const rtm_opts &op, const rtm_grid &gr, const Geo &g) {
 MigrationPlan plan_migration(const rtm_grid &gr, const rtm_acq &acq, const rtm_opts &op,
                              int nsample) {
   MigrationPlan p;
-  p.g = make_geo(gr);
+  p.g = make_geo(gr, 16);  // the shorter tile: the larger per-tile tables
   p.nsnap = gr.nt / op.isnap;
   const Geo &g = p.g;
   const int cpC = checkpoint_steps(op, gr, g);
@@ -268,6 +370,37 @@ static void sponge_profile(int N, int nb, std::vector<double> &out) {
   }
 }
 
+void sponge_tables(const Geo &g, std::vector<float> &gx, std::vector<float> &gz) {
+  std::vector<double> pz, px;
+  sponge_profile(g.NZ, g.nb, pz);
+  sponge_profile(g.NX, g.nb, px);
+  gz.assign(g.NZ, 0.f);
+  gx.assign(g.P, 0.f);
+  for (int I = 0; I < g.NZ; ++I) gz[I] = (float)pz[I];
+  for (int J = 0; J < g.NX; ++J) gx[g.X0 + J] = (float)px[J];
+}
+
+void receiver_tiles(const Geo &g, const rtm_acq &acq, std::vector<int> &rptr,
+                    std::vector<int2> &rent) {
+  const int ntiles = g.ntx * g.ntz;
+  rptr.assign(ntiles + 1, 0);
+  std::vector<int> rtile(acq.nrec);
+  for (int r = 0; r < acq.nrec; ++r) {
+    const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
+    rtile[r] = (row / TZ) * g.ntx + col / TX;
+    rptr[rtile[r] + 1]++;
+  }
+  for (int t = 0; t < ntiles; ++t) rptr[t + 1] += rptr[t];
+  rent.assign(std::max(acq.nrec, 1), make_int2(0, 0));
+  std::vector<int> fill(rptr.begin(), rptr.end() - 1);
+  for (int r = 0; r < acq.nrec; ++r) {
+    const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
+    const int t = rtile[r];
+    const int lr = row - (t / g.ntx) * TZ, lc = col - (t % g.ntx) * TX;
+    rent[fill[t]++] = make_int2(lr * TX + lc, r);
+  }
+}
+
 // ------------------------------------------------------- tensor maps --
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -308,6 +441,8 @@ struct Common {
   Geo g;
   Coef k;
   int nsample = 1;
+  int kernel = 3;  // RunConfig::step_kernel of the call
+  long long n_rent = 0, n_rext = 0, n_rcen = 0;  // receiver-table entries (debug index checks)
   DevBuf c_all, gx, gz, src_rc, rptr, rent, rext_ptr, rext_ent, rcen_ptr, rcen_ent, wav, items, err;
   CUtensorMap mc;
 };
@@ -318,7 +453,7 @@ struct Common {
 static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<int> &eptr,
                                  std::vector<int2> &eent, std::vector<int> &cptr,
                                  std::vector<int2> &cent) {
-  const int TXc = step2_tile_x(), TZc = step2_tile_z(), H = step2_ext(), EXw = TXc + 2 * H;
+  const int TXc = step2_tile_x(), TZc = g.tz2, H = step2_ext(), EXw = TXc + 2 * H;
   const int nt2 = g.ntx2 * g.ntz2;
   std::vector<std::vector<int2>> e(nt2), c(nt2);
   for (int r = 0; r < acq.nrec; ++r) {
@@ -349,45 +484,30 @@ static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<i
 
 // Upload the per-call tables shared by all items.
 static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
-                        int nsample, const float *vel_d, cudaStream_t st, int step_kernel) {
-  C.g = make_geo(gr);
+                        int nsample, const float *vel_d, cudaStream_t st, int step_kernel,
+                        int tile_z) {
+  C.g = make_geo(gr, step_kernel == 3 ? tile_z : 24);
+  C.kernel = step_kernel;
   C.k = make_coef(gr);
   C.nsample = nsample;
   const Geo &g = C.g;
-  std::vector<double> pz, px;
-  sponge_profile(g.NZ, g.nb, pz);
-  sponge_profile(g.NX, g.nb, px);
-  std::vector<float> gz(g.NZ), gx(g.P, 0.f);
-  for (int I = 0; I < g.NZ; ++I) gz[I] = (float)pz[I];
-  for (int J = 0; J < g.NX; ++J) gx[g.X0 + J] = (float)px[J];
+  std::vector<float> gz, gx;
+  sponge_tables(g, gx, gz);
   // sources: memory (row, col); receivers: CSR over single-step tiles
   std::vector<int> src(2 * acq.nshot);
   for (int s = 0; s < acq.nshot; ++s) {
     src[s] = acq.src_iz[s] + g.nb;
     src[acq.nshot + s] = acq.src_ix[s] + g.CP;
   }
-  const int ntiles = g.ntx * g.ntz;
-  std::vector<int> rptr(ntiles + 1, 0);
-  std::vector<int> rtile(acq.nrec);
-  for (int r = 0; r < acq.nrec; ++r) {
-    const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
-    rtile[r] = (row / TZ) * g.ntx + col / TX;
-    rptr[rtile[r] + 1]++;
-  }
-  for (int t = 0; t < ntiles; ++t) rptr[t + 1] += rptr[t];
-  std::vector<int2> rent(std::max(acq.nrec, 1));
-  {
-    std::vector<int> fill(rptr.begin(), rptr.end() - 1);
-    for (int r = 0; r < acq.nrec; ++r) {
-      const int row = acq.rec_iz[r] + g.nb, col = acq.rec_ix[r] + g.CP;
-      const int t = rtile[r];
-      const int lr = row - (t / g.ntx) * TZ, lc = col - (t % g.ntx) * TX;
-      rent[fill[t]++] = make_int2(lr * TX + lc, r);
-    }
-  }
+  std::vector<int> rptr;
+  std::vector<int2> rent;
+  receiver_tiles(g, acq, rptr, rent);
   std::vector<int> eptr, cptr;
   std::vector<int2> eent, cent;
   step2_receiver_lists(g, acq, eptr, eent, cptr, cent);
+  C.n_rent = (long long)rent.size();
+  C.n_rext = (long long)eent.size();
+  C.n_rcen = (long long)cent.size();
   CU(C.c_all.alloc(ctx, (size_t)nsample * g.plane * 4, st));
   CU(C.gx.alloc(ctx, gx.size() * 4, st));
   CU(C.gz.alloc(ctx, gz.size() * 4, st));
@@ -415,10 +535,10 @@ static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_a
   CU(cudaMemcpyAsync(C.wav.p, acq.wavelet, (size_t)gr.nt * 4, cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(C.err.p, 0, 16, st));
   CU(launch_prep_c(vel_d, C.c_all.as<float>(), g, gr.dt, nsample, st));
-  if (step_kernel == 2) {
+  if (step_kernel >= 2) {
     const int H = step2_ext();
     int rc = make_map(ctx, &C.mc, C.c_all.as<float>(), g, nsample, step2_tile_x() + 2 * H,
-                      step2_tile_z() + 2 * H);
+                      g.tz2 + 2 * H);
     if (rc) return rc;
   }
   // the host vectors above go out of scope: make the copies complete first
@@ -433,6 +553,7 @@ struct Fields {
   DevBuf v[2], d[2];
   CUtensorMap mv[2], md[2];
   int cv = 0, cd = 0;  // index of the current v and d buffer
+  int n2 = 0;          // two-step launches since the fields were zeroed (snake order parity)
 };
 
 static int alloc_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int B, cudaStream_t st,
@@ -440,13 +561,13 @@ static int alloc_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int B, cudaStream
   for (int i = 0; i < 2; ++i) {
     CU(F.v[i].alloc(ctx, (size_t)B * g.plane * 4, st));
     CU(F.d[i].alloc(ctx, (size_t)B * g.plane * 4, st));
-    if (step_kernel == 2) {
+    if (step_kernel >= 2) {
       const int H = step2_ext();
       int rc = make_map(ctx, &F.mv[i], F.v[i].as<float>(), g, B, step2_tile_x() + 4 * H,
-                        step2_tile_z() + 4 * H);
+                        g.tz2 + 4 * H);
       if (!rc)
         rc = make_map(ctx, &F.md[i], F.d[i].as<float>(), g, B, step2_tile_x() + 2 * H,
-                      step2_tile_z() + 2 * H);
+                      g.tz2 + 2 * H);
       if (rc) return rc;
     }
   }
@@ -458,7 +579,7 @@ static int zero_fields(rtm_ctx *ctx, Fields &F, const Geo &g, int nb, cudaStream
     CU(cudaMemsetAsync(F.v[i].p, 0, (size_t)nb * g.plane * 4, st));
     CU(cudaMemsetAsync(F.d[i].p, 0, (size_t)nb * g.plane * 4, st));
   }
-  F.cv = F.cd = 0;
+  F.cv = F.cd = F.n2 = 0;
   return RTM_OK;
 }
 
@@ -477,6 +598,11 @@ static void fill_args(StepArgs &A, const Common &C, const rtm_grid &gr, const rt
   A.rtile_ent = C.rent.as<int2>();
   A.nrec = acq.nrec;
   A.nt = gr.nt;
+  A.err = C.err.as<int>();
+  A.len.nshot = acq.nshot;
+  A.len.nsample = C.nsample;
+  A.len.rent = C.n_rent;
+  A.len.rcen = C.n_rcen;
 }
 
 static void fill_args2(Step2Args &A2, const StepArgs &A, const Common &C) {
@@ -509,6 +635,19 @@ static void fill_args2(Step2Args &A2, const StepArgs &A, const Common &C) {
   A2.den = A.den;
   A2.dmax = A.dmax;
   A2.err = C.err.as<int>();
+  A2.refl = A.refl;
+  A2.len = A.len;
+  A2.len.rent = C.n_rext;
+}
+
+// Test hook: if injections are pending, take one and raise this call's flag.
+static int maybe_inject_timeout(rtm_ctx *ctx, const Common &C, cudaStream_t st) {
+  int n = ctx->inject_timeouts.load();
+  while (n > 0 && !ctx->inject_timeouts.compare_exchange_weak(n, n - 1)) {
+  }
+  static const int kRaised = 1;  // (a pageable copy is staged before the call returns)
+  if (n > 0) CU(cudaMemcpyAsync(C.err.p, &kRaised, 4, cudaMemcpyHostToDevice, st));
+  return RTM_OK;
 }
 
 // One single-step launch: v from the current buffer into the other, d in place.
@@ -522,14 +661,22 @@ static int step1(rtm_ctx *ctx, int mode, StepArgs &A, Fields &F, const StepRT &r
   return RTM_OK;
 }
 
-// One two-step launch: both v and d into the other buffers.
+// One two-step launch: both v and d into the other buffers.  The persistent
+// kernel walks its tiles in snake order: every other launch from the end of
+// the tile list, so it starts on the grids the previous launch wrote last.
 static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields &F,
                  const Step2RT &rt, int nb, cudaStream_t st) {
   A2.v_out = F.v[1 - F.cv].as<float>();
   A2.d_out = F.d[1 - F.cd].as<float>();
-  CU(launch_step2(mode, F.mv[F.cv], F.md[F.cd], C.mc, A2, rt, nb, st));
+  Step2RT r = rt;
+  r.reverse = F.n2 & 1;
+  if (C.kernel == 3)
+    CU(launch_step2p(mode, C.g.tz2, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
+  else
+    CU(launch_step2(mode, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
   F.cv = 1 - F.cv;
   F.cd = 1 - F.cd;
+  F.n2 += 1;
   return RTM_OK;
 }
 
@@ -571,9 +718,10 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
                    int B, cudaStream_t st, const RunConfig &cfg, const float *born_refl,
-                   float *born_out, LateCopy *late) {
+                   float *born_out, LateCopy *late, int flag_slot) {
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel);
+  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z);
+  if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
   const Geo &g = C.g;
   const int nsnap = gr.nt / op.isnap;
@@ -679,9 +827,14 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   A.num = num.as<float>();
   A.den = den.as<float>();
   A.dmax = dmax.as<unsigned>();
+  A.len.items = B;
+  A.len.snap = (long long)B * ring * g.pplane;
+  A.len.smax = (long long)B * std::max(ring, 1);
+  A.len.refl = born_refl ? (long long)g.nz * g.nx : 0;
+  A.refl = born_refl;
   const int isnap = op.isnap, nt = gr.nt;
   const bool half = op.snap_dtype != RTM_SNAP_F32;
-  const bool two = cfg.step_kernel == 2;
+  const bool two = cfg.step_kernel >= 2;
   const bool graph = cfg.graph != 0;
   auto inK = [&](int m) { return m >= 1 && m <= nt && m % isnap == 0; };
   int nb = 0;
@@ -783,6 +936,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
         if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
         A.refl = A2.refl = born_refl;
         A.rec_out = A2.rec_out = born_out + (size_t)q0 * nt * acq.nrec;
+        A.len.rec_out = A2.len.rec_out = (nitems - q0) * (long long)nt * acq.nrec;
         if ((rc = mark())) return rc;
         rc = run_phase(ctx, graph, st, [&]() -> int {
           auto slot = [&](int k) { return inK(k) ? k / isnap - 1 : -1; };
@@ -849,7 +1003,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
       if ((rc = mark())) return rc;
     }
     CU(launch_norm_stack(A.num, A.den, A.dmax, A.item_sample, nb, (float)op.eps, g.pplane,
-                         stack.as<float>(), comp.as<float>(), st));
+                         stack.as<float>(), comp.as<float>(), nsample, C.err.as<int>(), st));
     launches += 1;
   }
   launches += step_launches;
@@ -860,7 +1014,8 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     launches += 1;
   }
   launches += 1;  // prep_c
-  CU(cudaMemcpyAsync(ctx->h_err, C.err.p, 4, cudaMemcpyDeviceToHost, st));
+  if (flag_slot >= 0)
+    CU(cudaMemcpyAsync(ctx->h_flags + 2 * flag_slot, C.err.p, 8, cudaMemcpyDeviceToHost, st));
   double ms_total = 0.0;
   if (ctx->prof) {
     CU(cudaStreamSynchronize(st));
@@ -888,10 +1043,11 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
 // (device), B shots advanced per launch.
 static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
                         const rtm_acq &acq, int s0, int ns, float *seis_d, int B,
-                        cudaStream_t st) {
+                        cudaStream_t st, int flag_slot) {
   const int sk = ctx->defaults.step_kernel;
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk);
+  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk, ctx->defaults.tile_z);
+  if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
   const Geo &g = C.g;
   if (B > ns) B = ns;
@@ -907,7 +1063,8 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
   if ((rc = alloc_fields(ctx, F, g, B, st, sk))) return rc;
   StepArgs A;
   fill_args(A, C, gr, acq);
-  const bool two = sk == 2;
+  A.len.items = B;
+  const bool two = sk >= 2;
   long long launches = 0;
   for (int q0 = 0; q0 < ns; q0 += B) {
     const int nb = std::min(B, ns - q0);
@@ -915,6 +1072,7 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
     A.item_sample = C.items.as<int>() + q0;
     A.item_shot = C.items.as<int>() + ns + q0;
     A.rec_out = seis_d + (size_t)q0 * gr.nt * acq.nrec;
+    A.len.rec_out = (long long)(ns - q0) * gr.nt * acq.nrec;
     Step2Args A2;
     fill_args2(A2, A, C);
     for (int n = 0; n < gr.nt;) {
@@ -937,7 +1095,8 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
       ++launches;
     }
   }
-  CU(cudaMemcpyAsync(ctx->h_err, C.err.p, 4, cudaMemcpyDeviceToHost, st));
+  if (flag_slot >= 0)
+    CU(cudaMemcpyAsync(ctx->h_flags + 2 * flag_slot, C.err.p, 8, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));  // `items` lives on this stack frame
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->stats.launches += launches + 1;
@@ -1009,15 +1168,11 @@ static int set_device(rtm_ctx *ctx) {
   return RTM_OK;
 }
 
-// A kernel whose bounded wait gave up leaves a flag that the call copies to
-// pinned host memory; it is reported by the call itself when that call
-// synchronises, else by the next call on the context.
-static int check_wait_flag(rtm_ctx *ctx) {
-  if (ctx->h_err && *(volatile int *)ctx->h_err) {
-    *ctx->h_err = 0;
-    return fail(ctx, RTM_ERR_TIMEOUT, "a device-side wait gave up in a previous launch");
-  }
-  return RTM_OK;
+// A call that synchronised its stream reads its own flag slot.
+static int own_wait_flag(rtm_ctx *ctx, int slot) {
+  int line = 0;
+  const int code = flag_take(ctx, slot, &line);
+  return flag_status(ctx, code, line, "this call");
 }
 
 }  // namespace rtm
@@ -1061,15 +1216,22 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
   }
   uint64_t thr = UINT64_MAX;
   cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  if (cudaMallocHost(&ctx->h_err, 16) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->h_flags, 2 * kFlagSlots * sizeof(int)) != cudaSuccess) {
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return RTM_ERR_CUDA;
   }
-  *ctx->h_err = 0;
-  // RTM_STEP_KERNEL=1 restricts propagation to the single-step kernel
+  for (int i = kFlagSlots - 1; i >= 0; --i) {
+    ctx->h_flags[2 * i] = ctx->h_flags[2 * i + 1] = 0;
+    ctx->free_flags.push_back(i);
+  }
+  // RTM_STEP_KERNEL=1 restricts propagation to the single-step kernel, =2 to
+  // the two-step kernel with one tile per block; otherwise the persistent
+  // two-step kernel is the default (RTM_TILE_Z=16 gives it 16-row tiles)
   const char *sk = std::getenv("RTM_STEP_KERNEL");
-  ctx->defaults.step_kernel = (sk && sk[0] == '1') ? 1 : 2;
+  ctx->defaults.step_kernel = (sk && sk[0] == '1') ? 1 : ((sk && sk[0] == '2') ? 2 : 3);
+  const char *tz = std::getenv("RTM_TILE_Z");
+  ctx->defaults.tile_z = (tz && std::atoi(tz) == 16 && ctx->defaults.step_kernel == 3) ? 16 : 24;
   // RTM_GRAPHS=1 captures each phase of a batch in a CUDA graph by default
   const char *gr = std::getenv("RTM_GRAPHS");
   ctx->defaults.graph = (gr && gr[0] == '1') ? 1 : 0;
@@ -1080,10 +1242,18 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
 int rtm_ctx_destroy(rtm_ctx *ctx) {
   if (!ctx) return RTM_OK;
   cudaSetDevice(ctx->device);
-  rtm_server_shutdown(ctx);
+  // requests still running after the shutdown bound keep using the context:
+  // leave it alive (the caller may try again) rather than free it under them
+  if (!rtm_server_shutdown(ctx))
+    return fail(ctx, RTM_ERR_BUSY, "requests are still running; the context was not destroyed");
   cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> lk(ctx->flag_mu);
+    for (auto &p : ctx->pending) cudaEventDestroy(p.ev);
+    ctx->pending.clear();
+  }
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
-  if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   delete ctx;
   return RTM_OK;
 }
@@ -1138,16 +1308,20 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
   int best = -1;
   double best_t = 1e300;
   std::vector<RunConfig> cand;
-  for (int sk : {2, 1})
+  // (kernel, tile height): persistent 24 and 16 rows, one tile per block, single step
+  const int kinds[4][2] = {{3, 24}, {3, 16}, {2, 24}, {1, 24}};
+  for (const auto &kd : kinds)
     for (int graph : {0, 1})
       for (long long items : {bmax, (bmax + 1) / 2}) {
         RunConfig c;
-        c.step_kernel = sk;
+        c.step_kernel = kd[0];
+        c.tile_z = kd[1];
         c.graph = graph;
         c.max_items = items >= nitems ? 0 : (int)items;
         bool dup = false;
         for (auto &o : cand)
-          dup |= o.step_kernel == c.step_kernel && o.graph == c.graph && o.max_items == c.max_items;
+          dup |= o.step_kernel == c.step_kernel && o.tile_z == c.tile_z && o.graph == c.graph &&
+                 o.max_items == c.max_items;
         if (!dup) cand.push_back(c);
       }
   rc = RTM_OK;
@@ -1186,11 +1360,17 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
       const int B = (int)((nitems + nbatch - 1) / nbatch);
       float ms = 0.f, best_ms = 1e30f;
       for (int rep = 0; rep < 3 && !rc; ++rep) {  // first run warms up
+        const int slot = flag_acquire(ctx);
         cudaEventRecord(e0, st);
         rc = migrate_device(ctx, tg, 1, vel.as<float>(), *acq, seis.as<float>(), to,
-                            img.as<float>(), B, st, c);
+                            img.as<float>(), B, st, c, nullptr, nullptr, nullptr, slot);
         cudaEventRecord(e1, st);
         if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, RTM_ERR_CUDA, "trial sync");
+        if (rc) {
+          flag_defer(ctx, slot, st);
+        } else {
+          rc = own_wait_flag(ctx, slot);
+        }
         if (!rc && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
           best_ms = std::min(best_ms, ms);
       }
@@ -1203,7 +1383,6 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
   vel.release();
   seis.release();
   img.release();
-  if (!rc) rc = check_wait_flag(ctx);
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(ctx, RTM_ERR_CUDA, "sync");
   unreserve(ctx, got);
   if (rc) return rc;
@@ -1215,6 +1394,7 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
     choice[0] = cand[best].step_kernel;
     choice[1] = cand[best].max_items;
     choice[2] = cand[best].graph;
+    choice[3] = cand[best].tile_z;
   }
   return RTM_OK;
 }
@@ -1232,6 +1412,12 @@ int rtm_selftest_wait(rtm_ctx *ctx, int wait_ms, int *raised, void *stream) {
   CU(cudaMemcpyAsync(&h, f.p, 4, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   *raised = h;
+  return RTM_OK;
+}
+
+int rtm_ctx_inject_wait_timeout(rtm_ctx *ctx, int count) {
+  if (!ctx || count < 0) return RTM_ERR_ARG;
+  ctx->inject_timeouts.store(count);
   return RTM_OK;
 }
 
@@ -1256,8 +1442,12 @@ int rtm_ctx_set_profiling(rtm_ctx *ctx, int on) {
 
 int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset) {
   if (!ctx || !out) return RTM_ERR_ARG;
+  long long peak = 0, backfilled = 0;
+  rtm_server_counters(ctx, reset != 0, &peak, &backfilled);
   std::lock_guard<std::mutex> lk(ctx->mu);
   *out = ctx->stats;
+  out->requests_peak_running = peak;
+  out->requests_backfilled = backfilled;
   if (reset) ctx->stats = rtm_stats{};
   return RTM_OK;
 }
@@ -1292,12 +1482,16 @@ int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_ac
   if (!got) return fail(ctx, RTM_ERR_TIMEOUT, "waited 600 s for device memory");
   const int B = (int)std::max<size_t>(1, std::min<size_t>(ns, (got - base) / item));
   View v, s;
+  const int slot = flag_acquire(ctx);
   rc = view_in(ctx, v, vel, vbytes, st);
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)grid->nx * grid->nz, st);
   if (!rc) rc = view_out(ctx, s, seis, sbytes, st);
-  if (!rc) rc = model_device(ctx, *grid, v.d, *acq, s0, ns, s.d, B, st);
+  if (!rc) rc = model_device(ctx, *grid, v.d, *acq, s0, ns, s.d, B, st, slot);
   if (!rc) rc = view_finish(ctx, s, seis, sbytes, st);
-  if (!rc) rc = check_wait_flag(ctx);  // model_device synchronised its stream
+  if (!rc)
+    rc = own_wait_flag(ctx, slot);  // model_device synchronised its stream
+  else
+    flag_defer(ctx, slot, st);
   unreserve(ctx, got);
   return rc;
 }
@@ -1344,6 +1538,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   const int B = (int)((nitems + nbatch - 1) / nbatch);
   View v, s, im;
   LateCopy late;
+  const int slot = flag_acquire(ctx);
   rc = view_in(ctx, v, vels, vbytes, st);
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
   // host seismograms: allocate now, upload behind the first forward phase
@@ -1353,10 +1548,13 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
   if (!rc)
     rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, op, im.d, B, st, cfg, nullptr,
-                        nullptr, s.staged ? &late : nullptr);
+                        nullptr, s.staged ? &late : nullptr, slot);
   late_end(late);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
-  if (!rc && (im.staged || ctx->prof)) rc = check_wait_flag(ctx);  // the stream was synchronised
+  if (!rc && (im.staged || ctx->prof))
+    rc = own_wait_flag(ctx, slot);  // the stream was synchronised
+  else
+    flag_defer(ctx, slot, st);
   unreserve(ctx, got);
   return rc;
 }
@@ -1411,15 +1609,19 @@ int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq
   const long long nbatch = (nitems + bmax - 1) / bmax;
   const int B = (int)((nitems + nbatch - 1) / nbatch);
   View v, m, out;
+  const int slot = flag_acquire(ctx);
   rc = view_in(ctx, v, vel, vbytes, st);
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)grid->nx * grid->nz, st);
   if (!rc) rc = view_in(ctx, m, refl, vbytes, st);
   if (!rc) rc = view_out(ctx, out, seis, sbytes, st);
   if (!rc)
     rc = migrate_device(ctx, *grid, 1, v.d, *acq, nullptr, *opts, nullptr, B, st, cfg, m.d,
-                        out.d);
+                        out.d, nullptr, slot);
   if (!rc) rc = view_finish(ctx, out, seis, sbytes, st);
-  if (!rc && (out.staged || ctx->prof)) rc = check_wait_flag(ctx);
+  if (!rc && (out.staged || ctx->prof))
+    rc = own_wait_flag(ctx, slot);
+  else
+    flag_defer(ctx, slot, st);
   unreserve(ctx, got);
   return rc;
 }

@@ -15,6 +15,39 @@
 
 namespace rtm {
 
+// Debug builds (-DRTM_DEBUG) check the index of every global access whose
+// offset the kernels compute from tables or launch scalars.  An index outside
+// its array skips the access, records the source line of the first failed
+// check in err[1] and raises err[0] = 2; nothing traps, so the context stays
+// usable and the call reports the failure.  Release builds compile the checks
+// away.
+#ifdef RTM_DEBUG
+__device__ __forceinline__ bool dbg_in(long long i, long long n, int *err, int line) {
+  if (i >= 0 && i < n) return true;
+  if (err) {
+    atomicCAS(err + 1, 0, line);
+    atomicExch(err, 2);
+  }
+  return false;
+}
+#define RTM_IN(i, n, err) ::rtm::dbg_in((long long)(i), (long long)(n), (err), __LINE__)
+#else
+#define RTM_IN(i, n, err) true
+#endif
+
+// Array lengths in elements, for the index checks of debug builds only.
+struct DbgLen {
+  long long items;    // item slots B: item tables, field planes, num / den planes, dmax
+  long long nshot;    // shots: source tables, seismogram shots
+  long long nsample;  // planes of c_all
+  long long snap;     // elements of snap
+  long long smax;     // entries of smax
+  long long rent;     // entries of rtile_ent / rext_ent
+  long long rcen;     // entries of rcen_ent
+  long long refl;     // elements of refl
+  long long rec_out;  // elements of rec_out
+};
+
 constexpr int TX = 128;   // tile width  (memory columns) of the step kernel
 constexpr int TZ = 32;    // tile height (rows)
 constexpr int HALO = 4;   // stencil radius (8th order)
@@ -26,7 +59,8 @@ struct Geo {
   int NZ, P, X0, NX, nb;  // padded grid
   int nz, nx, SX, CP;     // physical grid and its memory column origin
   int ntx, ntz;           // tiles per grid (single-step kernel)
-  int ntx2, ntz2;         // tiles per grid (two-step kernel)
+  int ntx2, ntz2;         // tiles per grid (two-step kernels)
+  int tz2;                // centre rows of a two-step tile (24, or 16 for the persistent kernel)
   long long plane;        // NZ * P   (floats)
   long long pplane;       // nz * SX  (elements)
 };
@@ -63,6 +97,8 @@ struct StepArgs {
   float *num, *den;          // [B][pplane] imaging accumulators
   unsigned *dmax;            // [B] max of den as float bits
   const float *refl;         // [nz][nx] reflectivity m of the Born operator
+  int *err;                  // debug builds: index-check flag (may be null)
+  DbgLen len;                // debug builds: array lengths
 };
 
 // Per-launch scalars.
@@ -104,8 +140,9 @@ struct Step2Args {
   unsigned *smax;
   float *num, *den;
   unsigned *dmax;
-  int *err;                      // set to 1 if a bounded wait gave up
+  int *err;                      // set to 1 if a bounded wait gave up (2: debug index check)
   const float *refl;             // [nz][nx] reflectivity of the Born operator
+  DbgLen len;                    // debug builds: array lengths
 };
 
 struct Step2RT {
@@ -118,6 +155,7 @@ struct Step2RT {
                        // inject c m S from this snapshot at substep 1
   int img_out_idx;     // image with the output field (backward); Born: at substep 2
   int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
+  int reverse;         // persistent kernel: walk the tile list from its end
 };
 
 enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2, MODE_BORN = 3 };

@@ -21,9 +21,11 @@ struct rtm_server;
 namespace rtm {
 // How a migration is launched (all choices give bit-identical results).
 struct RunConfig {
-  int step_kernel = 2;  // 2: two-step TMA kernel where possible; 1: single-step only
+  int step_kernel = 3;  // 3: persistent two-step kernel with a copy ring where possible;
+                        // 2: two-step kernel, one tile per block; 1: single-step only
   int max_items = 0;    // cap on items in flight (0 = memory budget)
   int graph = 0;        // 1: capture each phase of a batch in a CUDA graph
+  int tile_z = 24;      // centre rows of a two-step tile (16 only with step_kernel 3)
 };
 // Shape key of the autotuner cache.
 struct TuneKey {
@@ -49,14 +51,47 @@ struct rtm_ctx {
   bool prof = false;        // time the step-kernel phases with events
   rtm::RunConfig defaults;  // launch configuration when no tuned entry matches
   std::map<rtm::TuneKey, rtm::RunConfig> tuned;  // autotuner results (guarded by mu)
-  int *h_err = nullptr;     // pinned: device wait-timeout flag of the last call
+  // Device wait-timeout flags: one pinned slot per call in flight.  A call
+  // copies its kernels' flag into its own slot; a call that synchronises reads
+  // it, an asynchronous one leaves it pending with an event, and the next
+  // call on the context reads it once the event has completed.
+  struct PendingFlag {
+    int slot;
+    cudaEvent_t ev;
+  };
+  int *h_flags = nullptr;           // pinned [kFlagSlots][2]: {code, source line}
+  std::vector<int> free_flags;      // guarded by flag_mu
+  std::deque<PendingFlag> pending;  // guarded by flag_mu
+  int seen_code = 0, seen_line = 0;  // first raised flag among reaped pending ones (flag_mu)
+  std::mutex flag_mu;
+  std::atomic<int> inject_timeouts{0};  // test hook: calls that start with the flag raised
   rtm_stats stats{};        // guarded by mu
   rtm_server *server = nullptr;
 };
 
 namespace rtm {
 
+constexpr int kFlagSlots = 256;
+
 int fail(rtm_ctx *ctx, int code, const char *fmt, ...);
+// The message of the last fail() on the calling thread (request threads read
+// their own error text here, not the context's, which other threads share).
+const char *thread_error();
+
+// Device flag slots (see rtm_ctx).  A call's kernels raise its flag with
+// code 1 when a bounded wait gives up, and (debug builds) code 2 with the
+// source line when an index check fails.  Acquire a zeroed slot; copy the
+// call's two flag words into h_flags + 2 slot; after a synchronised call,
+// read and release it (flag_take: the code, 0 if none); or leave it pending
+// behind an event recorded on st.
+int flag_acquire(rtm_ctx *ctx);
+int flag_take(rtm_ctx *ctx, int slot, int *line);
+void flag_defer(rtm_ctx *ctx, int slot, cudaStream_t st);
+// The status a raised flag reports: RTM_ERR_TIMEOUT (a wait gave up) or
+// RTM_ERR_STATE (a debug index check failed); `whose` names the call.
+int flag_status(rtm_ctx *ctx, int code, int line, const char *whose);
+// An error status if a pending flag of an earlier call came back raised.
+int check_wait_flag(rtm_ctx *ctx);
 
 // Device allocation from the context pool, stream-ordered.
 struct DevBuf {
@@ -77,7 +112,14 @@ struct DevBuf {
 
 bool is_device_ptr(const void *p);
 
-Geo make_geo(const rtm_grid &gr);
+Geo make_geo(const rtm_grid &gr, int tile_z = 24);
+// Host tables of the propagation kernels: the sponge factors per memory column
+// (zero outside the padded domain) and per row (Cerjan profile, §3 reading);
+// the receivers of each single-step tile as CSR {row * TX + col in the tile,
+// receiver index}.
+void sponge_tables(const Geo &g, std::vector<float> &gx, std::vector<float> &gz);
+void receiver_tiles(const Geo &g, const rtm_acq &acq, std::vector<int> &rptr,
+                    std::vector<int2> &rent);
 int checkpoint_steps(const rtm_opts &op, const rtm_grid &gr, const Geo &g);
 Coef make_coef(const rtm_grid &gr);
 
@@ -118,11 +160,13 @@ struct LateCopy {
 // copy of the seismograms into seis_d is issued after the first forward
 // phase is enqueued, and the main stream waits for it before any backward
 // step.
+// The kernels' wait-timeout flag is copied into flag slot `flag_slot` (if
+// >= 0) once the work is enqueued.
 int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *vel_d,
                    const rtm_acq &acq, const float *seis_d, const rtm_opts &op, float *img_d,
                    int B, cudaStream_t st, const RunConfig &cfg,
                    const float *born_refl = nullptr, float *born_out = nullptr,
-                   LateCopy *late = nullptr);
+                   LateCopy *late = nullptr, int flag_slot = -1);
 RunConfig config_for(rtm_ctx *ctx, const rtm_grid &gr, const rtm_opts &op);
 
 // Velocity range check (CFL of §3, positivity, finiteness); synchronises st.
@@ -137,4 +181,10 @@ void unreserve(rtm_ctx *ctx, size_t bytes);
 // request loop (rtm_server.cu)
 int rtm_server_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket);
 int rtm_server_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms);
-void rtm_server_shutdown(rtm_ctx *ctx);
+// Cancels queued requests and waits (bounded) for running ones; false if some
+// are still running after the bound (the server then stays attached).
+bool rtm_server_shutdown(rtm_ctx *ctx);
+// Most requests running at once and requests admitted past a waiting head,
+// since the server started (or the last reset).
+void rtm_server_counters(rtm_ctx *ctx, bool reset, long long *peak_running,
+                         long long *backfilled);

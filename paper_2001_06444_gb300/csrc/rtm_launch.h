@@ -21,6 +21,13 @@ cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                          cudaStream_t st);
 size_t step2_smem_bytes();
+// persistent two-step kernel with a two-stage copy ring (rtm_prop2p.cu):
+// tile_z = 24 or 16 centre rows; maps with boxes (C2X + 16, tile_z + 16) for v
+// and (C2X + 8, tile_z + 8) for d and c; one block per resident slot
+cudaError_t launch_step2p(int mode, int tile_z, const CUtensorMap &mv, const CUtensorMap &md,
+                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
+                          cudaStream_t st);
+size_t step2p_smem_bytes(int tile_z);
 // bounded-wait self-test: raises *flag after waiting `ns` for bytes that never arrive
 cudaError_t launch_wait_probe(int *flag, unsigned long long ns, cudaStream_t st);
 int step2_tile_x();
@@ -30,9 +37,11 @@ int step2_ext();
 // imaging and statistics (rtm_post.cu)
 // Normalise each item's image (Eq. 5 with eps max(den)) and add it, in item
 // order, to its sample's Kahan-compensated stack; zero num and den.
+// (nsample: planes of the stacks; err: index-check flag of debug builds)
 cudaError_t launch_norm_stack(float *num, float *den, const unsigned *dmax,
                               const int *item_sample, int B, float eps, long long pplane,
-                              float *stack_all, float *comp_all, cudaStream_t st);
+                              float *stack_all, float *comp_all, int nsample, int *err,
+                              cudaStream_t st);
 // Final image of nsample samples: (optionally) the Laplacian filter of the
 // compensated stack, written compactly as [nsample][nz][nx].
 cudaError_t launch_filter(const float *stack_all, const float *comp_all, int nsample, int nz,

@@ -91,32 +91,13 @@ extern "C" int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const r
   if (!base) return RTM_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // host-side tables (pageable copies are staged before cudaMemcpyAsync returns)
-  std::vector<float> gx(g.P, 0.f), gz(g.NZ);
-  for (int I = 0; I < g.NZ; ++I) {
-    const int k = std::min(I, g.NZ - 1 - I);
-    gz[I] = k >= g.nb ? 1.f : (float)std::exp(-std::pow(0.015 * (g.nb - k), 2));
-  }
-  for (int J = 0; J < g.NX; ++J) {
-    const int k = std::min(J, g.NX - 1 - J);
-    gx[g.X0 + J] = k >= g.nb ? 1.f : (float)std::exp(-std::pow(0.015 * (g.nb - k), 2));
-  }
-  std::vector<int> rptr(ntiles + 1, 0), rtile(acq->nrec);
-  for (int r = 0; r < acq->nrec; ++r) {
-    const int row = acq->rec_iz[r] + g.nb, col = acq->rec_ix[r] + g.CP;
-    rtile[r] = (row / TZ) * g.ntx + col / TX;
-    rptr[rtile[r] + 1]++;
-  }
-  for (int t = 0; t < ntiles; ++t) rptr[t + 1] += rptr[t];
-  std::vector<int2> rent(std::max(acq->nrec, 1));
-  {
-    std::vector<int> fill(rptr.begin(), rptr.end() - 1);
-    for (int r = 0; r < acq->nrec; ++r) {
-      const int row = acq->rec_iz[r] + g.nb, col = acq->rec_ix[r] + g.CP;
-      const int t = rtile[r];
-      rent[fill[t]++] = make_int2((row - (t / g.ntx) * TZ) * TX + (col - (t % g.ntx) * TX), r);
-    }
-  }
+  // host-side tables, built as for the allocating entry points (pageable
+  // copies are staged before cudaMemcpyAsync returns)
+  std::vector<float> gx, gz;
+  sponge_tables(g, gx, gz);
+  std::vector<int> rptr;
+  std::vector<int2> rent;
+  receiver_tiles(g, *acq, rptr, rent);
   const int src[4] = {acq->src_iz[shot] + g.nb, acq->src_ix[shot] + g.CP, 0, 0};
   const unsigned rng0[4] = {0u, 0x7f7fffffu, 0u, 0u};
   auto E = [](cudaError_t e) { return e == cudaSuccess; };
@@ -170,6 +151,13 @@ extern "C" int rtm_model_noalloc(const rtm_grid *grid, const float *vel, const r
   A.nrec = acq->nrec;
   A.nt = grid->nt;
   A.rec_out = seis;
+  // lengths for the index checks of debug builds (which record nothing here:
+  // the call has no flag to report; a failed check only skips its access)
+  A.len.items = 1;
+  A.len.nshot = 1;
+  A.len.nsample = 1;
+  A.len.rent = (long long)rent.size();
+  A.len.rec_out = (long long)grid->nt * acq->nrec;
   float *fa = reinterpret_cast<float *>(base + o_fa), *fb = reinterpret_cast<float *>(base + o_fb);
   A.fd = reinterpret_cast<float *>(base + o_fd);
   StepRT rt{};

@@ -4,6 +4,7 @@
 
 #include <cmath>
 
+#include "rtm_common.h"
 #include "rtm_launch.h"
 
 namespace rtm {
@@ -14,13 +15,16 @@ namespace rtm {
 // cleared for the next batch.  One thread per 4 consecutive pixels.
 __global__ void k_norm_stack(float *num, float *den, const unsigned *dmax,
                              const int *item_sample, int B, float eps, long long pplane,
-                             float *stack_all, float *comp_all) {
+                             float *stack_all, float *comp_all, int nsample, int *err) {
   const long long e = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   if (e >= pplane) return;
+  (void)nsample;
+  (void)err;
   int cur = -1;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), cmp = acc;
   for (int b = 0; b < B; ++b) {
     const int smp = item_sample[b];
+    if (!RTM_IN(smp, nsample, err) || !RTM_IN(e + 3, pplane, err)) continue;
     if (smp != cur) {
       if (cur >= 0) {
         *reinterpret_cast<float4 *>(stack_all + cur * pplane + e) = acc;
@@ -192,10 +196,11 @@ __global__ void k_unc_maps(const double *mean, const double *std_, long long npi
 
 cudaError_t launch_norm_stack(float *num, float *den, const unsigned *dmax,
                               const int *item_sample, int B, float eps, long long pplane,
-                              float *stack_all, float *comp_all, cudaStream_t st) {
+                              float *stack_all, float *comp_all, int nsample, int *err,
+                              cudaStream_t st) {
   const long long n4 = pplane / 4;
-  k_norm_stack<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(num, den, dmax, item_sample, B,
-                                                             eps, pplane, stack_all, comp_all);
+  k_norm_stack<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(
+      num, den, dmax, item_sample, B, eps, pplane, stack_all, comp_all, nsample, err);
   return cudaGetLastError();
 }
 

@@ -124,13 +124,22 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
   __shared__ __align__(16) float s[SH][SW];
   __shared__ float red[STEP_THREADS / 32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int b = blockIdx.z;
   const Geo &g = A.g;
   const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+#ifdef RTM_DEBUG
+  // an item or sample outside its table is recorded; the block then works on
+  // item 0 / sample 0 instead of reading past the buffers
+  const int b = RTM_IN(blockIdx.z, A.len.items, A.err) ? (int)blockIdx.z : 0;
+  const int smp0 = A.item_sample[b];
+  const int smp = RTM_IN(smp0, A.len.nsample, A.err) ? smp0 : 0;
+#else
+  const int b = blockIdx.z;
+  const int smp = A.item_sample[b];
+#endif
   const float *__restrict__ cur = A.fa + (long long)b * g.plane;
   float *__restrict__ out = A.fb + (long long)b * g.plane;
   float *__restrict__ dd = A.fd + (long long)b * g.plane;
-  const float *__restrict__ cc = A.c_all + (long long)A.item_sample[b] * g.plane;
+  const float *__restrict__ cc = A.c_all + (long long)smp * g.plane;
 
   // 1. current field, tile + halo, into shared memory (zero beyond the buffer)
   constexpr int SW4 = SW / 4;
@@ -203,14 +212,16 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
   //     field at every physical pixel, on imaging steps
   const int j0 = col - g.CP;  // physical column of lane 0 (multiple of 4)
   const bool jok = j0 >= 0 && j0 < g.SX;
-  if (MODE == MODE_BORN && rt.img_idx >= 0 && jok) {
+  if (MODE == MODE_BORN && rt.img_idx >= 0 && jok &&
+      RTM_IN((long long)b * A.nsnap + rt.img_idx, A.len.smax, A.err)) {
     float sdq, inv;
     snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_idx], sdq, inv);
     const long long sbase = ((long long)b * A.nsnap + rt.img_idx) * g.pplane + j0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int i = row0 + r - g.nb;
-      if (i >= 0 && i < g.nz) {
+      if (i >= 0 && i < g.nz && RTM_IN(sbase + (long long)i * g.SX + 3, A.len.snap, A.err) &&
+          RTM_IN((long long)i * g.nx + min(j0 + 3, g.nx - 1), A.len.refl, A.err)) {
         const float4 S = snap_load4(A.snap, sbase + (long long)i * g.SX, A.snap_dtype, sdq);
         const float Sv[4] = {S.x, S.y, S.z, S.w};
 #pragma unroll
@@ -224,7 +235,15 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
 
   // 4. injection / recording through shared memory (only blocks that own
   //    a source or receiver cell; the condition is block-uniform)
+#ifdef RTM_DEBUG
+  const int shot0 = A.item_shot[b];
+  const bool shot_ok = RTM_IN(shot0, A.len.nshot, A.err) &&
+                       RTM_IN(blockIdx.y * g.ntx + blockIdx.x + 1, g.ntx * g.ntz + 1, A.err);
+  const int shot = shot_ok ? shot0 : 0;
+#else
   const int shot = A.item_shot[b];
+  constexpr bool shot_ok = true;
+#endif
   bool stage = false;
   int sr = -1, scl = -1, rp0 = 0, rp1 = 0;
   if (MODE == MODE_FWD || MODE == MODE_MODEL) {
@@ -235,7 +254,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
     else
       sr = -1;
   }
-  if (MODE != MODE_FWD) {
+  if (MODE != MODE_FWD && shot_ok) {
     const int tile = blockIdx.y * g.ntx + blockIdx.x;
     rp0 = A.rtile_ptr[tile];
     rp1 = A.rtile_ptr[tile + 1];
@@ -249,27 +268,35 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
           make_float4(res[r][0], res[r][1], res[r][2], res[r][3]);
     __syncthreads();
     if (MODE == MODE_FWD || MODE == MODE_MODEL) {
-      if (sr >= 0 && tid == 0) {
+      if (sr >= 0 && tid == 0 && RTM_IN(rt.n, A.nt, A.err)) {
         const long long o = (long long)(z0 + sr) * g.P + (x0 + scl);
         s[HALO + sr][HALO + scl] += cc[o] * (A.wav[rt.n] * A.src_scale);
       }
     } else if (MODE == MODE_BWD) {
-      const float *d = A.seis + ((long long)shot * A.nt + (rt.n - 1)) * A.nrec;
+      const long long d0 = ((long long)shot * A.nt + (rt.n - 1)) * A.nrec;
+      const float *d = A.seis + d0;
       for (int e = rp0 + tid; e < rp1; e += STEP_THREADS) {
+        if (!RTM_IN(e, A.len.rent, A.err)) continue;
         const int2 en = A.rtile_ent[e];
         const int lr = en.x / TX, lc = en.x - lr * TX;
         const long long o = (long long)(z0 + lr) * g.P + (x0 + lc);
-        atomicAdd(&s[HALO + lr][HALO + lc], cc[o] * d[en.y]);
+        if (RTM_IN(en.x, TX * TZ, A.err) && RTM_IN(o, g.plane, A.err) &&
+            RTM_IN(en.y, A.nrec, A.err) && RTM_IN(d0 + en.y, A.len.nshot * A.nt * A.nrec, A.err))
+          atomicAdd(&s[HALO + lr][HALO + lc], cc[o] * d[en.y]);
       }
     }
     __syncthreads();
     if (MODE == MODE_MODEL || MODE == MODE_BORN) {
-      float *ro = A.rec_out + ((long long)b * A.nt + rt.n) * A.nrec;
+      const long long r0 = ((long long)b * A.nt + rt.n) * A.nrec;
+      float *ro = A.rec_out + r0;
       for (int e = rp0 + tid; e < rp1; e += STEP_THREADS) {
+        if (!RTM_IN(e, A.len.rent, A.err)) continue;
         const int2 en = A.rtile_ent[e];
         const int lr = en.x / TX, lc = en.x - lr * TX;
         const long long o = (long long)(z0 + lr) * g.P + (x0 + lc);
-        ro[en.y] = cur[o] + s[HALO + lr][HALO + lc];  // v^{n+1} = v^n + d^{n+1}
+        if (RTM_IN(en.x, TX * TZ, A.err) && RTM_IN(o, g.plane, A.err) &&
+            RTM_IN(r0 + en.y, A.len.rec_out, A.err))
+          ro[en.y] = cur[o] + s[HALO + lr][HALO + lc];  // v^{n+1} = v^n + d^{n+1}
       }
     }
 #pragma unroll
@@ -299,7 +326,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
 
   // 6. forward: store the current field as a snapshot, reduce the new max
   if (MODE == MODE_FWD) {
-    if (rt.snap_idx >= 0 && jok) {
+    if (rt.snap_idx >= 0 && jok && RTM_IN((long long)b * A.nsnap + rt.snap_idx, A.len.smax, A.err)) {
       float sdq, inv;
       snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.snap_idx], sdq, inv);
       const long long base = ((long long)b * A.nsnap + rt.snap_idx) * g.pplane + j0;
@@ -311,7 +338,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
           if (j0 + 1 >= g.nx) v.y = 0.f;
           if (j0 + 2 >= g.nx) v.z = 0.f;
           if (j0 + 3 >= g.nx) v.w = 0.f;
-          snap_store4(A.snap, base + (long long)i * g.SX, A.snap_dtype, v, inv);
+          if (RTM_IN(base + (long long)i * g.SX + 3, A.len.snap, A.err))
+            snap_store4(A.snap, base + (long long)i * g.SX, A.snap_dtype, v, inv);
         }
       }
     }
@@ -324,14 +352,15 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
         for (int l = 0; l < 4; ++l)
           if (i >= 0 && i < g.nz && j0 + l >= 0 && j0 + l < g.nx) m = fmaxf(m, fabsf(res[r][l]));
       }
-      block_max_atomic(m, &A.smax[(long long)b * A.nsnap + rt.max_idx], red);
+      const long long k = (long long)b * A.nsnap + rt.max_idx;
+      block_max_atomic(m, &A.smax[RTM_IN(k, A.len.smax, A.err) ? k : 0], red);
     }
   }
 
   // 7. backward: imaging condition of Eq. 5 (numerator and illumination)
   if (MODE == MODE_BWD && rt.img_idx >= 0) {
     float dm = 0.f;
-    if (jok) {
+    if (jok && RTM_IN((long long)b * A.nsnap + rt.img_idx, A.len.smax, A.err)) {
       float sdq, inv;
       snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_idx], sdq, inv);
       const long long sbase = ((long long)b * A.nsnap + rt.img_idx) * g.pplane + j0;
@@ -339,7 +368,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int i = row0 + r - g.nb;
-        if (i >= 0 && i < g.nz) {
+        if (i >= 0 && i < g.nz && RTM_IN(sbase + (long long)i * g.SX + 3, A.len.snap, A.err) &&
+            RTM_IN(pbase + (long long)i * g.SX + 3, A.len.items * g.pplane, A.err)) {
           const float4 S = snap_load4(A.snap, sbase + (long long)i * g.SX, A.snap_dtype, sdq);
           float4 *pn = reinterpret_cast<float4 *>(A.num + pbase + (long long)i * g.SX);
           float4 *pd = reinterpret_cast<float4 *>(A.den + pbase + (long long)i * g.SX);

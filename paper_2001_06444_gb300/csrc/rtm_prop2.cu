@@ -39,17 +39,18 @@
 
 #include "rtm_common.h"
 #include "rtm_launch.h"
+#include "rtm_step2_dev.cuh"
 
 namespace rtm {
 
 namespace {
 
-constexpr int C2X = 120, C2Z = 24;           // centre tile
-constexpr int EX = C2X + 8, EZ = C2Z + 8;     // extended region (halo 4)
-constexpr int VX = C2X + 16, VZ = C2Z + 16;   // v^n tile (halo 8)
-constexpr int NTH = 256;                      // 32 x 8 threads
+using namespace s2;
+
+constexpr int C2Z = 24;                       // centre tile height
+constexpr int EZ = C2Z + 8;                   // extended region height (halo 4)
+constexpr int VZ = C2Z + 16;                  // v^n tile height (halo 8)
 constexpr unsigned kTxBytes = (VX * VZ + 2 * EX * EZ) * 4;
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of a device-side wait: 1 s
 
 struct Smem {
   float v0[VZ][VX];   // v^n            (TMA destination)
@@ -63,205 +64,6 @@ struct Smem {
 };
 static_assert(sizeof(float) * VX * VZ % 128 == 0, "tile offsets must stay 128-byte aligned");
 static_assert(sizeof(float) * EX * EZ % 128 == 0, "tile offsets must stay 128-byte aligned");
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ float lane4(const float4 &v, int l) {
-  return l == 0 ? v.x : (l == 1 ? v.y : (l == 2 ? v.z : v.w));
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for the mbarrier phase to complete, for at most `ns` nanoseconds.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase,
-                                                  unsigned long long ns) {
-  if (mbar_try_wait(bar, phase)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, phase))
-    if (global_ns() - t0 > ns) return false;
-  return true;
-}
-
-// Quantised store / load of 4 consecutive physical values (same encoding as
-// the single-step kernel).
-__device__ __forceinline__ void snap_store4(void *base, long long off, int dtype, float4 v,
-                                            float inv_s) {
-  if (dtype == 0) {
-    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + off) = v;
-  } else if (dtype == 2) {
-    __half2 a = __floats2half2_rn(v.x * inv_s, v.y * inv_s);
-    __half2 b = __floats2half2_rn(v.z * inv_s, v.w * inv_s);
-    uint2 u;
-    u.x = *reinterpret_cast<unsigned *>(&a);
-    u.y = *reinterpret_cast<unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(reinterpret_cast<__half *>(base) + off) = u;
-  } else {
-    __nv_bfloat162 a = __floats2bfloat162_rn(v.x * inv_s, v.y * inv_s);
-    __nv_bfloat162 b = __floats2bfloat162_rn(v.z * inv_s, v.w * inv_s);
-    uint2 u;
-    u.x = *reinterpret_cast<unsigned *>(&a);
-    u.y = *reinterpret_cast<unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(base) + off) = u;
-  }
-}
-
-__device__ __forceinline__ float4 snap_load4(const void *base, long long off, int dtype, float s) {
-  if (dtype == 0) return *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) + off);
-  uint2 u;
-  if (dtype == 2) {
-    u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __half *>(base) + off);
-    const float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
-    return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
-  }
-  u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + off);
-  const float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
-  const float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
-  return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
-}
-
-__device__ __forceinline__ void snap_scale(int dtype, unsigned mbits, float &s, float &inv) {
-  if (dtype == 0) {
-    s = inv = 1.f;
-    return;
-  }
-  const float m = __uint_as_float(mbits);
-  if (!(m > 0.f)) {
-    s = inv = 0.f;
-    return;
-  }
-  if (dtype == 2) {
-    s = m * (1.f / 32768.f);
-    inv = 32768.f / m;
-  } else {
-    s = m;
-    inv = 1.f / m;
-  }
-}
-
-__device__ __forceinline__ void block_max_atomic(float v, unsigned *dst, float *red) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (threadIdx.x == 0) red[threadIdx.y] = v;
-  __syncthreads();
-  if (threadIdx.y == 0) {
-    v = threadIdx.x < (NTH / 32) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-    for (int o = 4; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0 && v > 0.f) atomicMax(dst, __float_as_uint(v));
-  }
-}
-
-// Paired FP32 arithmetic (two lanes per instruction).  Each lane rounds
-// exactly like the scalar operation, so results equal the scalar kernel's;
-// a - b is formed as fma(b, -1, a), which rounds once like a subtraction.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-
-// One leapfrog update of 4 consecutive points in difference form.
-//   zc[0..8]: the 9 rows (centre row zc[4]) of the 4-column strip,
-//   xl, xr:   the 4 columns left and right of the strip in the centre row,
-//   dv, cv:   d^n and c at the strip,
-//   SPONGE:   the block's region reaches the sponge: every point takes the
-//             sponge form (which gives the interior formula's bits where
-//             g = 1), with gzr the row's factor and gxs the strip's four (in
-//             shared memory).  Blocks clear of the sponge compile in the
-//             interior formula alone.  (Choosing between the two forms per
-//             row measured slower.)
-// Returns d^{n+1} (before injection); v^{n+1} = v^n + d^{n+1}.  Lanes are
-// processed in pairs (0,1) and (2,3).
-template <bool SPONGE>
-__device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, const float4 &xr,
-                                          const float4 &dv, const float4 &cv, const Coef &k,
-                                          float gzr, const float *gxs) {
-  const float4 xc = zc[4];
-  const float v[12] = {xl.x, xl.y, xl.z, xl.w, xc.x, xc.y, xc.z, xc.w, xr.x, xr.y, xr.z, xr.w};
-  float out[4];
-#pragma unroll
-  for (int l = 0; l < 4; l += 2) {
-    const float2 ce = make_float2(v[4 + l], v[5 + l]);
-    float2 lap = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int m = 4; m >= 1; --m) {
-      const float2 xm = make_float2(v[4 + l - m], v[5 + l - m]);
-      const float2 xp = make_float2(v[4 + l + m], v[5 + l + m]);
-      const float2 tx = __fadd2_rn(sub2(xm, ce), sub2(xp, ce));
-      lap = __ffma2_rn(make_float2(k.ax[m - 1], k.ax[m - 1]), tx, lap);
-      const float2 zm = l == 0 ? make_float2(zc[4 - m].x, zc[4 - m].y)
-                               : make_float2(zc[4 - m].z, zc[4 - m].w);
-      const float2 zp = l == 0 ? make_float2(zc[4 + m].x, zc[4 + m].y)
-                               : make_float2(zc[4 + m].z, zc[4 + m].w);
-      const float2 tz = __fadd2_rn(sub2(zm, ce), sub2(zp, ce));
-      lap = __ffma2_rn(make_float2(k.az[m - 1], k.az[m - 1]), tz, lap);
-    }
-    const float2 c = l == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w);
-    const float2 p = l == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);
-    const float2 nd = __ffma2_rn(c, lap, p);
-    if (!SPONGE) {
-      out[l] = nd.x;
-      out[l + 1] = nd.y;
-    } else {
-      // g^2 d + g c L v - (1-g)^2 v, each lane rounded as the scalar form
-      // fmaf(g g, d, fmaf(g c, L v, (-(1-g)(1-g)) v)) of the single-step
-      // kernel; points with g == 1 take the interior formula
-      const float2 gg = __fmul2_rn(make_float2(gzr, gzr),
-                                   *reinterpret_cast<const float2 *>(gxs + l));
-      const float2 om = __ffma2_rn(gg, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
-      const float2 mo = __ffma2_rn(gg, make_float2(1.f, 1.f), make_float2(-1.f, -1.f));
-      const float2 w = __fmul2_rn(__fmul2_rn(om, mo), ce);
-      const float2 sp = __ffma2_rn(__fmul2_rn(gg, gg), p, __ffma2_rn(__fmul2_rn(gg, c), lap, w));
-      out[l] = gg.x == 1.f ? nd.x : sp.x;
-      out[l + 1] = gg.y == 1.f ? nd.y : sp.y;
-    }
-  }
-  return make_float4(out[0], out[1], out[2], out[3]);
-}
-
-// Born modelling: d += (c m) S at the physical pixels of a 4-column strip
-// (row i, columns j0..j0+3; j0 a multiple of 4) from snapshot idx; the same
-// rounding as the single-step kernel.
-__device__ __forceinline__ float4 born_inject4(const Step2Args &A, int b, int idx, int i, int j0,
-                                               float4 d, const float4 &c) {
-  const Geo &g = A.g;
-  if (idx < 0 || i < 0 || i >= g.nz || j0 < 0 || j0 >= g.SX) return d;
-  float sdq, inv;
-  snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + idx], sdq, inv);
-  const float4 S = snap_load4(A.snap, ((long long)b * A.nsnap + idx) * g.pplane +
-                                          (long long)i * g.SX + j0, A.snap_dtype, sdq);
-  const float *m = A.refl + (long long)i * g.nx + j0;
-  if (j0 < g.nx) d.x = fmaf(c.x * __ldg(m), S.x, d.x);
-  if (j0 + 1 < g.nx) d.y = fmaf(c.y * __ldg(m + 1), S.y, d.y);
-  if (j0 + 2 < g.nx) d.z = fmaf(c.z * __ldg(m + 2), S.z, d.z);
-  if (j0 + 3 < g.nx) d.w = fmaf(c.w * __ldg(m + 3), S.w, d.w);
-  return d;
-}
 
 // Substep 1: (v^{n+1}, d^{n+1}) on the extended region, rows 4ty..4ty+3 and
 // columns 4tx..4tx+3 of it, into S.d and S.v1.
@@ -359,6 +161,15 @@ __global__ void __launch_bounds__(NTH, 3)
   const int x0 = blockIdx.x * C2X, z0 = blockIdx.y * C2Z;
   const int smp = A.one_sample ? 0 : A.item_sample[b];  // c tile's sample, before the copies
   const int shot = A.item_shot[b];
+#ifdef RTM_DEBUG
+  // block-level indices of the debug checks (the copy engine zero-fills a
+  // plane outside the c map, so a bad sample is recorded, not read)
+  const bool shot_ok = RTM_IN(b, A.len.items, A.err) && RTM_IN(smp, A.len.nsample, A.err) &&
+                       RTM_IN(shot, A.len.nshot, A.err) &&
+                       RTM_IN(blockIdx.y * g.ntx2 + blockIdx.x + 1, g.ntx2 * g.ntz2 + 1, A.err);
+#else
+  constexpr bool shot_ok = true;
+#endif
 
   // blocks whose extended region stays clear of the sponge (g = 1 there)
   const bool interior = (z0 - 4 >= g.nb) && (z0 + C2Z + 4 <= g.NZ - g.nb) &&
@@ -423,7 +234,10 @@ __global__ void __launch_bounds__(NTH, 3)
   // reduced by the launch that produced it)
   if (MODE == MODE_FWD && rt.snap_in_idx >= 0 && wide) {
     float sdq, inv;
-    snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.snap_in_idx], sdq, inv);
+    snap_scale(A.snap_dtype,
+               A.smax[RTM_IN((long long)b * A.nsnap + rt.snap_in_idx, A.len.smax, A.err)
+                          ? (long long)b * A.nsnap + rt.snap_in_idx : 0],
+               sdq, inv);
     const int j0 = x0 + 4 * tx - g.CP;
     if (j0 >= 0 && j0 < g.SX) {
       const long long base = ((long long)b * A.nsnap + rt.snap_in_idx) * g.pplane + j0;
@@ -435,7 +249,8 @@ __global__ void __launch_bounds__(NTH, 3)
           if (j0 + 1 >= g.nx) v.y = 0.f;
           if (j0 + 2 >= g.nx) v.z = 0.f;
           if (j0 + 3 >= g.nx) v.w = 0.f;
-          snap_store4(A.snap, base + (long long)i * g.SX, A.snap_dtype, v, inv);
+          if (RTM_IN(base + (long long)i * g.SX + 3, A.len.snap, A.err))
+            snap_store4(A.snap, base + (long long)i * g.SX, A.snap_dtype, v, inv);
         }
       }
     }
@@ -459,23 +274,28 @@ __global__ void __launch_bounds__(NTH, 3)
     if (MODE == MODE_FWD || MODE == MODE_MODEL) {
       const int sr = A.src_row[shot] - (z0 - 4), sc = A.src_col[shot] - (x0 - 4);
       if (sr >= 0 && sr < EZ && sc >= 0 && sc < EX) {  // block-uniform
-        if (tid == 0) {
+        if (tid == 0 && RTM_IN(rt.t1, A.nt, A.err)) {
           S.d[sr][sc] += S.c[sr][sc] * (A.wav[rt.t1] * A.src_scale);
           S.v1[sr][sc] = S.v0[sr + 4][sc + 4] + S.d[sr][sc];
         }
         __syncthreads();
       }
     } else if (MODE == MODE_BWD) {
-      const int p0 = A.rext_ptr[tile], p1 = A.rext_ptr[tile + 1];
+      const int p0 = shot_ok ? A.rext_ptr[tile] : 0, p1 = shot_ok ? A.rext_ptr[tile + 1] : 0;
       if (p1 > p0) {  // block-uniform
-        const float *dsamp = A.seis + ((long long)shot * A.nt + rt.t1) * A.nrec;
+        const long long d0 = ((long long)shot * A.nt + rt.t1) * A.nrec;
+        const float *dsamp = A.seis + d0;
         for (int e = p0 + tid; e < p1; e += NTH) {
+          if (!RTM_IN(e, A.len.rent, A.err)) continue;
           const int2 en = A.rext_ent[e];
           const int er = en.x / EX, ec = en.x - er * EX;
-          atomicAdd(&S.d[er][ec], S.c[er][ec] * dsamp[en.y]);
+          if (RTM_IN(en.x, EX * EZ, A.err) && RTM_IN(en.y, A.nrec, A.err) &&
+              RTM_IN(d0 + en.y, A.len.nshot * A.nt * A.nrec, A.err))
+            atomicAdd(&S.d[er][ec], S.c[er][ec] * dsamp[en.y]);
         }
         __syncthreads();
         for (int e = p0 + tid; e < p1; e += NTH) {
+          if (!RTM_IN(e, A.len.rent, A.err) || !RTM_IN(A.rext_ent[e].x, EX * EZ, A.err)) continue;
           const int2 en = A.rext_ent[e];
           const int er = en.x / EX, ec = en.x - er * EX;
           S.v1[er][ec] = S.v0[er + 4][ec + 4] + S.d[er][ec];  // duplicates write equal values
@@ -488,11 +308,14 @@ __global__ void __launch_bounds__(NTH, 3)
   // step-(n+1) work on the centre: recording, FP32 snapshot, imaging
   if (MODE == MODE_MODEL || MODE == MODE_BORN) {
     const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
-    const int p0 = A.rcen_ptr[tile], p1 = A.rcen_ptr[tile + 1];
-    float *ro = A.rec_out + ((long long)b * A.nt + rt.t1) * A.nrec;
+    const int p0 = shot_ok ? A.rcen_ptr[tile] : 0, p1 = shot_ok ? A.rcen_ptr[tile + 1] : 0;
+    const long long r0 = ((long long)b * A.nt + rt.t1) * A.nrec;
+    float *ro = A.rec_out + r0;
     for (int e = p0 + tid; e < p1; e += NTH) {
+      if (!RTM_IN(e, A.len.rcen, A.err)) continue;
       const int2 en = A.rcen_ent[e];
-      ro[en.y] = (&S.v1[0][0])[en.x];
+      if (RTM_IN(en.x, EX * EZ, A.err) && RTM_IN(r0 + en.y, A.len.rec_out, A.err))
+        ro[en.y] = (&S.v1[0][0])[en.x];
     }
   }
   const int j0 = x0 + 4 * tx - g.CP;  // physical column of this thread's strip
@@ -508,11 +331,13 @@ __global__ void __launch_bounds__(NTH, 3)
         if (j0 + 1 >= g.nx) v.y = 0.f;
         if (j0 + 2 >= g.nx) v.z = 0.f;
         if (j0 + 3 >= g.nx) v.w = 0.f;
-        snap_store4(A.snap, base + (long long)i * g.SX, 0, v, 1.f);
+        if (RTM_IN(base + (long long)i * g.SX + 3, A.len.snap, A.err))
+          snap_store4(A.snap, base + (long long)i * g.SX, 0, v, 1.f);
       }
     }
   }
-  if (MODE == MODE_BWD && rt.img_mid_idx >= 0 && jok) {
+  if (MODE == MODE_BWD && rt.img_mid_idx >= 0 && jok &&
+      RTM_IN((long long)b * A.nsnap + rt.img_mid_idx, A.len.smax, A.err)) {
     float sdq, inv;
     snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_mid_idx], sdq, inv);
     const long long sbase = ((long long)b * A.nsnap + rt.img_mid_idx) * g.pplane + j0;
@@ -520,7 +345,8 @@ __global__ void __launch_bounds__(NTH, 3)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int i = z0 + 3 * ty + r - g.nb;
-      if (i >= 0 && i < g.nz) {
+      if (i >= 0 && i < g.nz && RTM_IN(sbase + (long long)i * g.SX + 3, A.len.snap, A.err) &&
+          RTM_IN(pbase + (long long)i * g.SX + 3, A.len.items * g.pplane, A.err)) {
         const float4 w = *reinterpret_cast<const float4 *>(&S.v1[4 + 3 * ty + r][4 + 4 * tx]);
         const float4 Sv = snap_load4(A.snap, sbase + (long long)i * g.SX, A.snap_dtype, sdq);
         float4 *pn = reinterpret_cast<float4 *>(A.num + pbase + (long long)i * g.SX);
@@ -540,7 +366,8 @@ __global__ void __launch_bounds__(NTH, 3)
       }
     }
   }
-  if (MODE == MODE_BWD && rt.dmax_flag == 1) block_max_atomic(dm, &A.dmax[b], S.red);
+  if (MODE == MODE_BWD && rt.dmax_flag == 1)
+    block_max_atomic(dm, &A.dmax[RTM_IN(b, A.len.items, A.err) ? b : 0], S.red);
 
   // ---- 3. substep 2 on the centre (rows 3ty..3ty+2, cols 4tx..4tx+3) -------
   float4 res[3];
@@ -569,7 +396,7 @@ __global__ void __launch_bounds__(NTH, 3)
       else
         sr = -1;
     }
-    if (MODE != MODE_FWD) {
+    if (MODE != MODE_FWD && shot_ok) {
       p0 = A.rcen_ptr[tile];
       p1 = A.rcen_ptr[tile + 1];
       if (p1 > p0) stage = true;
@@ -583,21 +410,28 @@ __global__ void __launch_bounds__(NTH, 3)
       }
       __syncthreads();
       if (MODE == MODE_FWD || MODE == MODE_MODEL) {
-        if (sr >= 0 && tid == 0)
+        if (sr >= 0 && tid == 0 && RTM_IN(rt.t2, A.nt, A.err))
           S.d[4 + sr][4 + sc] += S.c[4 + sr][4 + sc] * (A.wav[rt.t2] * A.src_scale);
       } else if (MODE == MODE_BWD) {
-        const float *dsamp = A.seis + ((long long)shot * A.nt + rt.t2) * A.nrec;
+        const long long d0 = ((long long)shot * A.nt + rt.t2) * A.nrec;
+        const float *dsamp = A.seis + d0;
         for (int e = p0 + tid; e < p1; e += NTH) {
+          if (!RTM_IN(e, A.len.rcen, A.err)) continue;
           const int2 en = A.rcen_ent[e];
-          atomicAdd(&(&S.d[0][0])[en.x], (&S.c[0][0])[en.x] * dsamp[en.y]);
+          if (RTM_IN(en.x, EX * EZ, A.err) && RTM_IN(en.y, A.nrec, A.err) &&
+              RTM_IN(d0 + en.y, A.len.nshot * A.nt * A.nrec, A.err))
+            atomicAdd(&(&S.d[0][0])[en.x], (&S.c[0][0])[en.x] * dsamp[en.y]);
         }
       }
       __syncthreads();
       if (MODE == MODE_MODEL || MODE == MODE_BORN) {
-        float *ro = A.rec_out + ((long long)b * A.nt + rt.t2) * A.nrec;
+        const long long r0 = ((long long)b * A.nt + rt.t2) * A.nrec;
+        float *ro = A.rec_out + r0;
         for (int e = p0 + tid; e < p1; e += NTH) {
+          if (!RTM_IN(e, A.len.rcen, A.err)) continue;
           const int2 en = A.rcen_ent[e];
-          ro[en.y] = (&S.v1[0][0])[en.x] + (&S.d[0][0])[en.x];  // v^{n+2} = v^{n+1} + d^{n+2}
+          if (RTM_IN(en.x, EX * EZ, A.err) && RTM_IN(r0 + en.y, A.len.rec_out, A.err))
+            ro[en.y] = (&S.v1[0][0])[en.x] + (&S.d[0][0])[en.x];  // v^{n+2} = v^{n+1} + d^{n+2}
         }
       }
       if (wide) {
@@ -619,7 +453,9 @@ __global__ void __launch_bounds__(NTH, 3)
       const int row = z0 + 3 * ty + r;
       const float4 nv = make_float4(cen[r].x + res[r].x, cen[r].y + res[r].y, cen[r].z + res[r].z,
                                     cen[r].w + res[r].w);
-      if (row < g.NZ && col < g.P) {
+      if (row < g.NZ && col < g.P &&
+          RTM_IN((long long)b * g.plane + (long long)row * g.P + col + 3, A.len.items * g.plane,
+                 A.err)) {
         const long long o = (long long)row * g.P + col;
         *reinterpret_cast<float4 *>(dq + o) = res[r];
         *reinterpret_cast<float4 *>(vo + o) = nv;
@@ -632,7 +468,9 @@ __global__ void __launch_bounds__(NTH, 3)
           for (int l = 0; l < 4; ++l)
             if (j0 + l >= 0 && j0 + l < g.nx) mx = fmaxf(mx, fabsf(lane4(nv, l)));
         }
-        if (MODE == MODE_FWD && rt.snap_out_idx >= 0 && jok) {
+        if (MODE == MODE_FWD && rt.snap_out_idx >= 0 && jok &&
+            RTM_IN(((long long)b * A.nsnap + rt.snap_out_idx) * g.pplane + (long long)i * g.SX + j0 + 3,
+                   A.len.snap, A.err)) {
           float4 v = nv;
           if (j0 + 1 >= g.nx) v.y = 0.f;
           if (j0 + 2 >= g.nx) v.z = 0.f;
@@ -641,7 +479,12 @@ __global__ void __launch_bounds__(NTH, 3)
                                   (long long)i * g.SX + j0,
                       0, v, 1.f);
         }
-        if (MODE == MODE_BWD && rt.img_out_idx >= 0 && jok) {
+        if (MODE == MODE_BWD && rt.img_out_idx >= 0 && jok &&
+            RTM_IN((long long)b * A.nsnap + rt.img_out_idx, A.len.smax, A.err) &&
+            RTM_IN(((long long)b * A.nsnap + rt.img_out_idx) * g.pplane + (long long)i * g.SX + j0 + 3,
+                   A.len.snap, A.err) &&
+            RTM_IN((long long)b * g.pplane + (long long)i * g.SX + j0 + 3, A.len.items * g.pplane,
+                   A.err)) {
           float sdq, inv;
           snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_out_idx], sdq, inv);
           const float4 Sv =
@@ -667,9 +510,12 @@ __global__ void __launch_bounds__(NTH, 3)
       }
     }
   }
-  if (MODE == MODE_FWD && rt.max_out_idx >= 0)
-    block_max_atomic(mx, &A.smax[(long long)b * A.nsnap + rt.max_out_idx], S.red);
-  if (MODE == MODE_BWD && rt.dmax_flag == 2) block_max_atomic(dm, &A.dmax[b], S.red);
+  if (MODE == MODE_FWD && rt.max_out_idx >= 0) {
+    const long long k = (long long)b * A.nsnap + rt.max_out_idx;
+    block_max_atomic(mx, &A.smax[RTM_IN(k, A.len.smax, A.err) ? k : 0], S.red);
+  }
+  if (MODE == MODE_BWD && rt.dmax_flag == 2)
+    block_max_atomic(dm, &A.dmax[RTM_IN(b, A.len.items, A.err) ? b : 0], S.red);
 }
 
 // Self-test of the bounded wait: one block arms an mbarrier for bytes that no

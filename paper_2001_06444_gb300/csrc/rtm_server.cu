@@ -5,9 +5,13 @@
 // memory budget can hold its snapshot buffers (at least one shot in flight,
 // up to all of its shots), gives it its own CUDA stream and a launcher thread,
 // and moves on: requests that arrive while others run join the device work as
-// memory frees up, and their kernels overlap on the GPU.  Admission is strictly
-// in order (no request overtakes an earlier one), so nothing starves.  Every
-// wait is bounded; a request that fails reports FAILED with its error text.
+// memory frees up, and their kernels overlap on the GPU.
+//
+// Backfill: while the head waits for memory, a later request that fits in
+// what is free now is admitted past it, up to kMaxOvertake times per head;
+// after that the head is admitted before anything else, so nothing starves.
+// Every wait is bounded; a request that fails reports FAILED with its own
+// error text (a device-side wait that gave up fails its own request only).
 //
 // The paper runs independent migrations in MPI subgroups, starting the next
 // one as soon as a subgroup finishes (§3); this is the single-GPU counterpart.
@@ -29,6 +33,7 @@ struct rtm_req_state {
   std::vector<float> wav;
   MigrationPlan plan;
   size_t need1 = 0, want = 0, reserved = 0;
+  int overtaken = 0;  // later requests admitted while this one headed the queue
   int state = RTM_REQ_QUEUED;
   int rc = RTM_OK;
   std::string err;
@@ -43,8 +48,12 @@ struct rtm_server {
   bool stop = false;
   uint64_t next = 1;
   int running = 0;
+  int peak_running = 0;  // most requests running at once
+  long long backfilled = 0;  // requests admitted past a waiting head
   static constexpr int kMaxQueue = 4096;
   static constexpr int kMaxRunning = 32;
+  static constexpr int kMaxOvertake = 16;    // backfill admissions past one waiting head
+  static constexpr int kBackfillWindow = 64;  // queued requests looked at behind the head
 };
 
 static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_state> q, int B) {
@@ -56,10 +65,15 @@ static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_sta
     rc = RTM_ERR_CUDA;
     err = "could not create a stream for the request";
   }
+  // this request's own wait-timeout flag and error text (other request
+  // threads share the context's)
+  const int slot = rc ? -1 : flag_acquire(ctx);
   if (!rc) rc = check_velocity(ctx, q->r.grid, q->r.vel, (long long)q->r.grid.nx * q->r.grid.nz, st);
   if (!rc)
     rc = migrate_device(ctx, q->r.grid, 1, q->r.vel, q->r.acq, q->r.seis, q->r.opts, q->r.image,
-                        B, st, config_for(ctx, q->r.grid, q->r.opts));
+                        B, st, config_for(ctx, q->r.grid, q->r.opts), nullptr, nullptr, nullptr,
+                        slot);
+  if (rc && err.empty()) err = thread_error();
   if (st) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) {
@@ -68,9 +82,11 @@ static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_sta
     }
     cudaStreamDestroy(st);
   }
-  if (rc && err.empty()) {
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    err = ctx->err;
+  int line = 0;
+  const int code = flag_take(ctx, slot, &line);
+  if (code && !rc) {
+    rc = flag_status(ctx, code, line, "this request (its image is incomplete)");
+    err = thread_error();
   }
   unreserve(ctx, q->reserved);
   {
@@ -81,6 +97,30 @@ static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_sta
     S->running--;
   }
   S->cv.notify_all();
+}
+
+// Start request q with `got` bytes reserved (S->mu held; q already out of
+// the queue).
+static void admit(rtm_ctx *ctx, rtm_server *S, const std::shared_ptr<rtm_req_state> &q, size_t got) {
+  q->reserved = got;
+  q->state = RTM_REQ_RUNNING;
+  S->running++;
+  S->peak_running = std::max(S->peak_running, S->running);
+  const long long nitems = q->r.acq.nshot;
+  long long B = (long long)((got - q->plan.shared_bytes) / q->plan.item_bytes);
+  B = std::max<long long>(1, std::min<long long>(B, nitems));
+  std::thread(run_request, ctx, S, q, (int)B).detach();
+  S->cv.notify_all();
+}
+
+// Remove q from the queue if it is still there (S->mu held).
+static bool take_from_queue(rtm_server *S, const std::shared_ptr<rtm_req_state> &q) {
+  for (auto it = S->queue.begin(); it != S->queue.end(); ++it)
+    if (*it == q) {
+      S->queue.erase(it);
+      return true;
+    }
+  return false;
 }
 
 static void scheduler(rtm_ctx *ctx, rtm_server *S) {
@@ -95,16 +135,33 @@ static void scheduler(rtm_ctx *ctx, rtm_server *S) {
     lk.unlock();
     const size_t got = reserve_wait(ctx, q->want, q->need1, 20);
     lk.lock();
-    if (!got) continue;  // head of the queue waits for memory; retry
-    S->queue.pop_front();
-    q->reserved = got;
-    q->state = RTM_REQ_RUNNING;
-    S->running++;
-    const long long nitems = q->r.acq.nshot;
-    long long B = (long long)((got - q->plan.shared_bytes) / q->plan.item_bytes);
-    B = std::max<long long>(1, std::min<long long>(B, nitems));
-    std::thread(run_request, ctx, S, q, (int)B).detach();
-    S->cv.notify_all();
+    if (got) {
+      if (take_from_queue(S, q))
+        admit(ctx, S, q, got);
+      else
+        unreserve(ctx, got);  // cancelled by a shutdown meanwhile
+      continue;
+    }
+    // the head waits for memory: backfill with a later request that fits in
+    // what is free now, a bounded number of times per head
+    if (q->overtaken >= rtm_server::kMaxOvertake) continue;
+    std::vector<std::shared_ptr<rtm_req_state>> behind;
+    for (size_t i = 1; i < S->queue.size() && (int)i <= rtm_server::kBackfillWindow; ++i)
+      behind.push_back(S->queue[i]);
+    for (auto &c : behind) {
+      if (S->stop || S->running >= rtm_server::kMaxRunning) break;
+      lk.unlock();
+      const size_t g2 = reserve_wait(ctx, c->want, c->need1, 0);
+      lk.lock();
+      if (!g2) continue;
+      if (take_from_queue(S, c)) {
+        q->overtaken++;
+        S->backfilled++;
+        admit(ctx, S, c, g2);
+        break;
+      }
+      unreserve(ctx, g2);
+    }
   }
 }
 
@@ -154,6 +211,7 @@ int rtm_server_submit(rtm_ctx *ctx, const rtm_request *req, uint64_t *ticket) {
   rtm_server *S = ensure_server(ctx);
   {
     std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return fail(ctx, RTM_ERR_STATE, "the context is being destroyed");
     if ((int)S->queue.size() >= rtm_server::kMaxQueue)
       return fail(ctx, RTM_ERR_BUSY, "request queue is full (%d)", rtm_server::kMaxQueue);
     q->id = S->next++;
@@ -187,9 +245,9 @@ int rtm_server_poll(rtm_ctx *ctx, uint64_t ticket, int *state, int timeout_ms) {
   return RTM_OK;
 }
 
-void rtm_server_shutdown(rtm_ctx *ctx) {
+bool rtm_server_shutdown(rtm_ctx *ctx) {
   rtm_server *S = ctx->server;
-  if (!S) return;
+  if (!S) return true;
   {
     std::unique_lock<std::mutex> lk(S->mu);
     // cancel what never started; wait (bounded) for running requests
@@ -204,7 +262,27 @@ void rtm_server_shutdown(rtm_ctx *ctx) {
   }
   S->cv.notify_all();
   if (S->sched.joinable()) S->sched.join();
-  const bool idle = S->running == 0;
+  bool idle;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    idle = S->running == 0;
+  }
+  if (!idle) return false;  // requests still running after the bound keep S (and ctx) alive
   ctx->server = nullptr;
-  if (idle) delete S;  // a request still running after the bound keeps S alive
+  delete S;
+  return true;
+}
+
+void rtm_server_counters(rtm_ctx *ctx, bool reset, long long *peak_running,
+                         long long *backfilled) {
+  *peak_running = *backfilled = 0;
+  rtm_server *S = ctx->server;
+  if (!S) return;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *peak_running = S->peak_running;
+  *backfilled = S->backfilled;
+  if (reset) {
+    S->peak_running = S->running;
+    S->backfilled = 0;
+  }
 }

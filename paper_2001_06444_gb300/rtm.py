@@ -30,7 +30,8 @@ EXPORTS = ("rtm_ctx_create", "rtm_ctx_destroy", "rtm_ctx_set_batch", "rtm_ctx_se
            "rtm_migrate_ensemble", "rtm_born", "rtm_migrate_adjoint", "rtm_lsrtm",
            "rtm_ensemble_stats",
            "rtm_uncertainty_maps",
-           "rtm_submit", "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait", "rtm_compress_bound",
+           "rtm_submit", "rtm_poll", "rtm_model_noalloc", "rtm_selftest_wait",
+           "rtm_ctx_inject_wait_timeout", "rtm_compress_bound",
            "rtm_compress", "rtm_decompress", "rtm_eikonal", "rtm_last_error", "rtm_cfl_limit")
 
 
@@ -66,7 +67,8 @@ class Stats(C.Structure):
                 ("codec_launches", C.c_longlong), ("codec_ms", C.c_double),
                 ("codec_bytes", C.c_double), ("eik_launches", C.c_longlong),
                 ("eik_ms", C.c_double), ("eik_updates", C.c_double),
-                ("graph_launches", C.c_longlong)]
+                ("graph_launches", C.c_longlong), ("requests_peak_running", C.c_longlong),
+                ("requests_backfilled", C.c_longlong)]
 
 
 class Request(C.Structure):
@@ -79,11 +81,12 @@ _lock = threading.Lock()
 
 
 def lib():
-    """The loaded CUDA library (built on first use)."""
+    """The loaded CUDA library (built on first use).  With RTM_DEBUG=1 in the
+    environment, the bounds-checked build instead."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=os.environ.get("RTM_DEBUG") == "1")
             L = C.CDLL(path)
             vp, ip = C.c_void_p, C.c_int
             L.rtm_ctx_create.argtypes = [C.POINTER(vp), ip, C.c_size_t]
@@ -112,6 +115,7 @@ def lib():
             L.rtm_autotune.argtypes = [vp, C.POINTER(Grid), C.POINTER(Acq), C.POINTER(Opts), ip,
                                        C.POINTER(C.c_int), vp]
             L.rtm_selftest_wait.argtypes = [vp, ip, C.POINTER(ip), vp]
+            L.rtm_ctx_inject_wait_timeout.argtypes = [vp, ip]
             L.rtm_model_noalloc.argtypes = [C.POINTER(Grid), vp, C.POINTER(Acq), ip, vp, vp]
             ll, u64 = C.c_longlong, C.c_uint64
             L.rtm_compress_bound.argtypes = [ll, ll]
@@ -258,10 +262,15 @@ class Context:
     def autotune(self, grid: Grid, acq: Acq, opts: Opts, trial_steps: int = 64) -> dict:
         """Time the launch configurations on short synthetic trials and keep
         the fastest for this shape; returns it."""
-        ch = (C.c_int * 3)()
+        ch = (C.c_int * 4)()
         self._check(lib().rtm_autotune(self.h, C.byref(grid), C.byref(acq), C.byref(opts),
                                        int(trial_steps), ch, C.c_void_p(0)))
-        return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2]}
+        return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2], "tile_z": ch[3]}
+
+    def inject_wait_timeout(self, count: int = 1):
+        """The next `count` migration or modelling calls start with their
+        wait-timeout flag raised (test hook of the failure reporting)."""
+        self._check(lib().rtm_ctx_inject_wait_timeout(self.h, int(count)))
 
     def selftest_wait(self, wait_ms: int = 200) -> bool:
         """Run the bounded device-side wait on a barrier nothing completes;

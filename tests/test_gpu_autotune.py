@@ -1,6 +1,7 @@
 """The launch-configuration autotuner and graph-captured batches: every
-candidate configuration (time-block depth, items in flight, CUDA graph
-capture) must give bit-identical images, so tuning never changes a result."""
+candidate configuration (propagation kernel and tile height, items in
+flight, CUDA graph capture) must give bit-identical images, so tuning never
+changes a result."""
 import os
 
 import numpy as np
@@ -45,7 +46,9 @@ def test_autotune_and_graph_capture_are_bitwise_neutral(dtype):
     with rtm.Context(0) as ctx:
         base = _migrate(ctx, s, v, seis, opts)
         choice = ctx.autotune(rtm.make_grid(*s.grid_tuple()), acq, opts, trial_steps=40)
-        assert choice["step_kernel"] in (1, 2) and choice["graph"] in (0, 1)
+        assert choice["step_kernel"] in (1, 2, 3) and choice["graph"] in (0, 1)
+        assert choice["tile_z"] in (16, 24) and (choice["tile_z"] == 24 or
+                                                 choice["step_kernel"] == 3)
         assert choice["max_items"] >= 0
         assert np.array_equal(_migrate(ctx, s, v, seis, opts), base)
         assert np.array_equal(_migrate(ctx, s, v, seis, opts, side), base)

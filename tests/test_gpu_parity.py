@@ -337,16 +337,37 @@ def test_full_size_sampled_parity(ctx):
     assert rel_l2(g48, oi) <= IMG_TOL
 
 
+def _env_context(**env):
+    """A context created with the given environment variables set (they pick
+    the context's default propagation kernel and tile height)."""
+    import os
+
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: str(v) for k, v in env.items()})
+    try:
+        return rtm.Context(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+
+
+# the two-step kernels: one tile per block; persistent with 24- and 16-row tiles
+TWO_STEP_KERNELS = [dict(RTM_STEP_KERNEL=2), dict(RTM_STEP_KERNEL=3),
+                    dict(RTM_STEP_KERNEL=3, RTM_TILE_Z=16)]
+
+
 @pytest.mark.parametrize("nz", [90, 47])
-def test_two_step_kernel_matches_single_step_bitwise(ctx, nz):
-    """The two-step TMA kernel and the single-step kernel compute the same
+def test_two_step_kernel_matches_single_step_bitwise(nz):
+    """The two-step TMA kernels (one tile per block; persistent with a copy
+    ring, 24- and 16-row tiles) and the single-step kernel compute the same
     per-point arithmetic in the same order, so modelling and migration agree
     bit for bit (every snapshot format, even and odd isnap, odd nt, sponge
     widths that are not multiples of 4).  With nz = 47 the padded grid has
     73 rows, so the last row of 24-row tiles holds one row of the grid and
     most of its warps skip both substeps."""
-    import os
-
     nx, nt = 250, 301
     v = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=21, water_depth=80.0)
     s = inputs.Survey(nx, nz, 13, 10.0, 10.0, 1e-3, nt, v, np.array([3, 120, 247], np.int32),
@@ -354,25 +375,65 @@ def test_two_step_kernel_matches_single_step_bitwise(ctx, nz):
                       np.full(nx, 1, np.int32), inputs.ricker(20.0, 1e-3, nt))
     data = np.stack([ora_model(s, v, k) for k in range(3)])
     vm = inputs.smooth(v, 10.0, 10.0, 30.0)
-    old = os.environ.get("RTM_STEP_KERNEL")
-    os.environ["RTM_STEP_KERNEL"] = "1"
+    one = _env_context(RTM_STEP_KERNEL=1)
     try:
-        one = rtm.Context(0)
-    finally:
-        if old is None:
-            del os.environ["RTM_STEP_KERNEL"]
-        else:
-            os.environ["RTM_STEP_KERNEL"] = old
-    try:
-        for shot in range(3):
-            assert np.array_equal(gpu_model(one, s, v, shot), gpu_model(ctx, s, v, shot))
-        for isnap, mode in ((4, rtm.SNAP_F32), (3, rtm.SNAP_F32), (1, rtm.SNAP_F32),
-                            (4, rtm.SNAP_F16), (2, rtm.SNAP_BF16), (3, rtm.SNAP_F16)):
-            a = gpu_migrate(one, s, vm, data, isnap=isnap, dtype=mode)
-            b = gpu_migrate(ctx, s, vm, data, isnap=isnap, dtype=mode)
-            assert np.array_equal(a, b), (isnap, mode)
+        ref_model = [gpu_model(one, s, v, shot) for shot in range(3)]
+        cases = ((4, rtm.SNAP_F32), (3, rtm.SNAP_F32), (1, rtm.SNAP_F32),
+                 (4, rtm.SNAP_F16), (2, rtm.SNAP_BF16), (3, rtm.SNAP_F16))
+        ref_img = [gpu_migrate(one, s, vm, data, isnap=i, dtype=m) for i, m in cases]
     finally:
         one.close()
+    for env in TWO_STEP_KERNELS:
+        two = _env_context(**env)
+        try:
+            for shot in range(3):
+                assert np.array_equal(gpu_model(two, s, v, shot), ref_model[shot]), (env, shot)
+            for (isnap, mode), want in zip(cases, ref_img):
+                got = gpu_migrate(two, s, vm, data, isnap=isnap, dtype=mode)
+                assert np.array_equal(got, want), (env, isnap, mode)
+        finally:
+            two.close()
+
+
+def test_persistent_kernel_many_tiles_bitwise():
+    """A batch with several times more tiles than the persistent kernel keeps
+    resident (24 shots of a 640 x 187 grid: 1440 or 2160 tiles per launch),
+    so every block walks several tiles through both stages of its copy ring,
+    in both snake directions, and receivers lie in tiles at block boundaries.
+    Modelling of all shots side by side and migration in every snapshot
+    format must equal the one-tile-per-block kernel bit for bit."""
+    nx, nz, nt = 640, 187, 160
+    v = inputs.layered_faulted(nz, nx, 10.0, 10.0, seed=77, water_depth=60.0)
+    ns = 24
+    s = inputs.Survey(nx, nz, 20, 10.0, 10.0, 1e-3, nt, v,
+                      np.linspace(5, nx - 6, ns).astype(np.int32), np.full(ns, 2, np.int32),
+                      np.arange(0, nx, 2, dtype=np.int32), np.full(nx // 2, 3, np.int32),
+                      inputs.ricker(18.0, 1e-3, nt))
+    seis = (inputs.normal(9, ns * nt * s.nrec).reshape(ns, nt, s.nrec) * 1e-3).astype(np.float32)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+
+    def run(c):
+        out = torch.zeros((ns, nt, s.nrec), dtype=torch.float32, device="cuda")
+        c.model(rtm.make_grid(*s.grid_tuple()), dev(v), acq, -1, out)
+        imgs = [gpu_migrate(c, s, v, seis, isnap=i, dtype=m)
+                for i, m in ((4, rtm.SNAP_F32), (2, rtm.SNAP_F16), (4, rtm.SNAP_BF16))]
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), imgs
+
+    ref = None
+    for env in TWO_STEP_KERNELS:
+        c = _env_context(**env)
+        try:
+            got = run(c)
+        finally:
+            c.close()
+        if ref is None:
+            ref = got
+            continue
+        assert np.array_equal(got[0], ref[0]), env
+        for a, b in zip(got[1], ref[1]):
+            assert np.array_equal(a, b), env
 
 
 def test_full_size_ensemble_sampled_parity(ctx):

@@ -89,3 +89,56 @@ def test_precision_sweep(ctx, problem, isnap):
     print(f"isnap {isnap}: " + ", ".join(
         f"{['f32', 'bf16', 'f16'][m]} img {r[0]:.2e}/{r[2]:.2e} std {r[1]:.2e}/{r[3]:.2e}"
         for m, r in report.items()))
+
+
+def test_full_size_half_precision_parity(ctx):
+    """Half-precision snapshots at the full 1701 x 351, 5000-step size
+    (isnap 4), where per-snapshot max scaling meets the 10 Hz fields' full
+    dynamic range.  One shot migrated with FP16 and with BF16 snapshots
+    against the oracle replaying the same quantisation (1e-2), its error
+    against exact snapshots reported; then the std map of 4 velocity samples
+    x that shot in each format against the oracle's std map (2e-2)."""
+    s = inputs.full_size(nshot=96)
+    shot = 47
+    one = inputs.Survey(s.nx, s.nz, s.nb, s.dx, s.dz, s.dt, s.nt, s.vel, s.src_ix[shot:shot + 1],
+                        s.src_iz[shot:shot + 1], s.rec_ix, s.rec_iz, s.wavelet)
+    g = oracle.grid(*one.grid_tuple())
+    w = one.wavelet.astype(np.float32).astype(np.float64)
+    data = oracle.model(g, s.vel.astype(np.float32).astype(np.float64), one.src_ix[0],
+                        one.src_iz[0], one.rec_ix, one.rec_iz, w).astype(np.float32)[None]
+    vm = inputs.smooth(s.vel, s.dx, s.dz, 60.0).astype(np.float32)
+    ens = inputs.ensemble(vm, s.dx, s.dz, 4).astype(np.float32)
+    keep = rtm._Keep()
+    acq = rtm.make_acq(keep, one.src_ix, one.src_iz, one.rec_ix, one.rec_iz,
+                       one.wavelet.astype(np.float32))
+    grid = rtm.make_grid(*one.grid_tuple())
+
+    def ora(vel, mode):
+        return oracle.migrate(g, vel.astype(np.float64), one.src_ix, one.src_iz, one.rec_ix,
+                              one.rec_iz, w, data.astype(np.float64), isnap=4, snap_mode=mode)
+
+    exact = ora(vm, 0)
+    report = {}
+    for mode in (rtm.SNAP_F16, rtm.SNAP_BF16):
+        img = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+        ctx.migrate(grid, torch.from_numpy(vm).cuda(), acq, torch.from_numpy(data).cuda(),
+                    rtm.Opts(4, mode, 1e-6, 1), img)
+        imgs = torch.zeros((4, s.nz, s.nx), dtype=torch.float32, device="cuda")
+        ctx.migrate_ensemble(grid, torch.from_numpy(ens).cuda(), acq,
+                             torch.from_numpy(data).cuda(), rtm.Opts(4, mode, 1e-6, 1), imgs)
+        outs = [torch.zeros(s.nz * s.nx, dtype=t, device="cuda")
+                for t in (torch.float64, torch.float64, torch.float32, torch.float32)]
+        ctx.ensemble_stats(imgs, *outs)
+        torch.cuda.synchronize()
+        got = img.cpu().numpy()
+        want = ora(vm, mode)
+        _, want_std, _, _ = oracle.ensemble_stats(
+            np.stack([ora(ens[i], mode) for i in range(4)]).reshape(4, -1))
+        e_img = rel_l2(got, want)
+        e_std = rel_l2(outs[1].cpu().numpy(), want_std)
+        report[mode] = (e_img, rel_l2(got, exact), e_std, rel_l2(want, exact))
+        assert e_img <= IMG_TOL[mode], (mode, e_img)
+        assert e_std <= STD_TOL, (mode, e_std)
+    print("full size, isnap 4: " + ", ".join(
+        f"{['f32', 'bf16', 'f16'][m]} img {r[0]:.2e} vs replay / {r[1]:.2e} vs exact "
+        f"(oracle replay vs exact {r[3]:.2e}), std {r[2]:.2e}" for m, r in report.items()))

@@ -59,6 +59,9 @@ def test_mixed_requests_match_direct_migration():
         for t, r, w in zip(tickets, reqs, want):
             assert states[t] == rtm.REQ_DONE
             assert np.array_equal(r["img"].cpu().numpy(), w)
+        # the requests ran side by side (each on its own stream), not one
+        # after another
+        assert ctx.stats()["requests_peak_running"] >= 2
     finally:
         ctx.close()
 
@@ -94,6 +97,46 @@ def test_admission_runs_one_at_a_time_under_a_small_budget():
             time.sleep(0.005)
         assert len(done) == len(tickets)
         assert running_seen <= 1
+        assert ctx.stats()["requests_peak_running"] <= 1
+        torch.cuda.synchronize()
+        for r, w in zip(reqs, want):
+            assert np.array_equal(r["img"].cpu().numpy(), w)
+    finally:
+        ctx.close()
+
+
+def test_backfill_admits_a_small_request_past_a_waiting_head():
+    """A long request holds most of the budget; the next one in the queue
+    cannot start until it ends, but a small one behind it fits in what is
+    left.  The small one is admitted past the waiting head and finishes while
+    the long one still runs; every image equals the direct call's."""
+    long_r = _request(201, 101, 4, 24000, 21)
+    head = _request(601, 301, 2, 2000, 22)
+    small = _request(161, 81, 1, 300, 23)
+    cb = {}
+    for name, r in (("long", long_r), ("head", head), ("small", small)):
+        call_b, item_b = rtm.plan_bytes(r["grid"], r["acq"], r["opts"])
+        cb[name] = (call_b, item_b)
+    want_long = cb["long"][0] + 4 * cb["long"][1]
+    need_head = cb["head"][0] + cb["head"][1]
+    need_small = cb["small"][0] + cb["small"][1]
+    assert need_head > need_small
+    ctx = rtm.Context(0, budget_bytes=want_long + need_small + (need_head - need_small) // 2)
+    try:
+        reqs = [long_r, head, small]
+        want = [_direct(ctx, r) for r in reqs]
+        for r in reqs:
+            r["img"].zero_()
+        torch.cuda.synchronize()
+        ctx.stats(reset=True)
+        tickets = [ctx.submit(r["req"]) for r in reqs]
+        st, _ = ctx.poll(tickets[2], 120000)
+        assert st == rtm.REQ_DONE
+        st_long, _ = ctx.poll(tickets[0], 0)
+        assert st_long == rtm.REQ_RUNNING  # the small request overtook the head
+        states = _wait(ctx, tickets[:2])
+        assert all(v == rtm.REQ_DONE for v in states.values())
+        assert ctx.stats()["requests_backfilled"] >= 1
         torch.cuda.synchronize()
         for r, w in zip(reqs, want):
             assert np.array_equal(r["img"].cpu().numpy(), w)
