@@ -34,6 +34,8 @@ from paper_2001_06444_gb300.sharding import barrier, max_over_ranks  # noqa: E40
 METRIC = "RTM shots/s & Gpt-updates/s vs HBM roofline; p50/p99 latency, mixed stream"
 WORKLOAD = "rtm_1701x351_96shots_nt5000_isnap4_f32snap"
 STEP_KERNEL_NAMES = {
+    4: "k_step2a (two-step TMA kernel, one tile per block, v^{n+1} over v^n; forward+backward "
+       "phases)",
     3: "k_step2p (persistent two-step TMA kernel, two-stage copy ring; forward+backward phases)",
     2: "k_step2 (two-step TMA kernel, one tile per block; forward+backward phases)",
     1: "k_step (single-step kernel; forward+backward phases)",
@@ -49,13 +51,15 @@ def parse():
     p.add_argument("--batch", type=int, default=0, help="items in flight (0 = memory budget)")
     # a fixed launch configuration instead of the autotuner's choice (for
     # comparisons and profiler captures of one kernel)
-    p.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+    p.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
                    help="0 autotune; 1 single-step; 2 two-step, one tile per block; "
-                        "3 persistent two-step")
-    p.add_argument("--tile-z", type=int, default=24, choices=[16, 24],
-                   help="with --kernel 3: centre rows of a tile")
+                        "3 persistent two-step; 4 two-step, one tile per block, v^{n+1} over v^n")
+    p.add_argument("--tile-z", type=int, default=24, choices=[16, 24, 32],
+                   help="with --kernel 3 (16, 24) or 4 (24, 32): centre rows of a tile")
     p.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                    help="with --kernel 1-3: capture each phase in a CUDA graph")
+    p.add_argument("--l2-ahead", type=int, default=0, choices=[0, 1],
+                   help="with --kernel 2: each block prefetches a later block's tile into L2")
     p.add_argument("--snap", default="f32", choices=["f32", "bf16", "f16"])
     p.add_argument("--checkpoint", type=int, default=0,
                    help="0 keep every snapshot; C>0 / -1 recompute from checkpoints")
@@ -237,6 +241,7 @@ def run_native(args, world, rank, local):
         os.environ["RTM_STEP_KERNEL"] = str(args.kernel)
         os.environ["RTM_TILE_Z"] = str(args.tile_z)
         os.environ["RTM_GRAPHS"] = str(args.graphs)
+        os.environ["RTM_L2_AHEAD"] = str(args.l2_ahead)
     ctx = rtm.Context(local)
     ctx.model(grid, vel_true, acq, -1, seis)  # observed data, untimed
     torch.cuda.synchronize()
@@ -244,7 +249,8 @@ def run_native(args, world, rank, local):
         ctx.set_batch(args.batch)
     if args.kernel:
         tuned = {"step_kernel": args.kernel, "max_items": args.batch, "graph": args.graphs,
-                 "tile_z": args.tile_z if args.kernel == 3 else 24, "fixed": True}
+                 "tile_z": args.tile_z if args.kernel in (3, 4) else 24,
+                 "l2_ahead": args.l2_ahead if args.kernel == 2 else 0, "fixed": True}
     else:
         tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
     for _ in range(args.warmup):

@@ -175,18 +175,23 @@ int rtm_ctx_stats(rtm_ctx *ctx, rtm_stats *out, int reset);
 /* Choose how migrations shaped like (grid, acq, opts) are launched on this
  * context, by timing short trial migrations (trial_steps time steps, 64 if
  * <= 0) of every candidate on synthetic inputs:
- *   - the propagation kernel and its tile: the persistent two-step kernel
- *     (kernel 3: two blocks per SM walk the tile list, the copies of the next
- *     tile overlapping the current one) with 120 x 24 or 120 x 16 centre
- *     tiles, the two-step kernel with one 120 x 24 tile per block (kernel 2),
- *     or the single-step kernel (kernel 1);
+ *   - the propagation kernel and its tile: the two-step kernel with one
+ *     120 x 24 tile per block (kernel 2), with or without each block
+ *     prefetching into L2 the tile that a later block will load; the
+ *     persistent two-step kernel (kernel 3: two blocks per SM walk the tile
+ *     list, the copies of the next tile overlapping the current one) with
+ *     120 x 24 or 120 x 16 centre tiles; the two-step kernel with one tile
+ *     per block that writes v^{n+1} over v^n in shared memory (kernel 4),
+ *     which fits 120 x 24 or 120 x 32 tiles at 3 blocks per SM; or the
+ *     single-step kernel (kernel 1);
  *   - the number of migrations in flight;
  *   - whether each phase of a batch is captured and replayed as a CUDA graph.
  * The fastest is used by later rtm_migrate, rtm_migrate_ensemble and
  * request-loop calls with the same grid, nt, isnap and snapshot format.  All
  * candidates give bit-identical results.
- * choice (nullable, 4 ints): {kernel 1, 2 or 3, items cap (0 = memory),
- * graph 0 or 1, tile height 24 or 16}.  Synchronises the stream. */
+ * choice (nullable, 5 ints): {kernel 1 to 4, items cap (0 = memory), graph 0
+ * or 1, tile height 16, 24 or 32, L2 prefetch 0 or 1}.  Synchronises the
+ * stream. */
 int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq,
                  const rtm_opts *opts, int trial_steps, int *choice, void *stream);
 

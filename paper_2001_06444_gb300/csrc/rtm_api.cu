@@ -203,9 +203,11 @@ Coef make_coef(const rtm_grid &gr) {
   Coef k;
   const double rx = 1.0 / (gr.dx * gr.dx), rz = 1.0 / (gr.dz * gr.dz);
   k.c0 = (float)(kA8[0] * (rx + rz));
+  k.iso = 1;
   for (int m = 1; m <= 4; ++m) {
     k.ax[m - 1] = (float)(kA8[m] * rx);
     k.az[m - 1] = (float)(kA8[m] * rz);
+    k.iso &= k.ax[m - 1] == k.az[m - 1];
   }
   return k;
 }
@@ -441,7 +443,8 @@ struct Common {
   Geo g;
   Coef k;
   int nsample = 1;
-  int kernel = 3;  // RunConfig::step_kernel of the call
+  int kernel = 2;  // RunConfig::step_kernel of the call
+  int l2_ahead = 0;  // RunConfig::l2_ahead of the call
   long long n_rent = 0, n_rext = 0, n_rcen = 0;  // receiver-table entries (debug index checks)
   DevBuf c_all, gx, gz, src_rc, rptr, rent, rext_ptr, rext_ent, rcen_ptr, rcen_ent, wav, items, err;
   CUtensorMap mc;
@@ -485,9 +488,10 @@ static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<i
 // Upload the per-call tables shared by all items.
 static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
                         int nsample, const float *vel_d, cudaStream_t st, int step_kernel,
-                        int tile_z) {
-  C.g = make_geo(gr, step_kernel == 3 ? tile_z : 24);
+                        int tile_z, int l2_ahead) {
+  C.g = make_geo(gr, step_kernel >= 3 ? tile_z : 24);
   C.kernel = step_kernel;
+  C.l2_ahead = l2_ahead;
   C.k = make_coef(gr);
   C.nsample = nsample;
   const Geo &g = C.g;
@@ -668,10 +672,15 @@ static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields 
                  const Step2RT &rt, int nb, cudaStream_t st) {
   A2.v_out = F.v[1 - F.cv].as<float>();
   A2.d_out = F.d[1 - F.cd].as<float>();
+  A2.v_in = F.v[F.cv].as<float>();
+  A2.d_in = F.d[F.cd].as<float>();
   Step2RT r = rt;
   r.reverse = F.n2 & 1;
+  r.ahead = C.l2_ahead;
   if (C.kernel == 3)
     CU(launch_step2p(mode, C.g.tz2, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
+  else if (C.kernel == 4)
+    CU(launch_step2a(mode, C.g.tz2, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
   else
     CU(launch_step2(mode, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
   F.cv = 1 - F.cv;
@@ -720,7 +729,8 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
                    int B, cudaStream_t st, const RunConfig &cfg, const float *born_refl,
                    float *born_out, LateCopy *late, int flag_slot) {
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z);
+  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z,
+                        cfg.l2_ahead);
   if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
   const Geo &g = C.g;
@@ -1046,7 +1056,8 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
                         cudaStream_t st, int flag_slot) {
   const int sk = ctx->defaults.step_kernel;
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk, ctx->defaults.tile_z);
+  int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk, ctx->defaults.tile_z,
+                        ctx->defaults.l2_ahead);
   if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
   const Geo &g = C.g;
@@ -1225,13 +1236,19 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->h_flags[2 * i] = ctx->h_flags[2 * i + 1] = 0;
     ctx->free_flags.push_back(i);
   }
-  // RTM_STEP_KERNEL=1 restricts propagation to the single-step kernel, =2 to
-  // the two-step kernel with one tile per block; otherwise the persistent
-  // two-step kernel is the default (RTM_TILE_Z=16 gives it 16-row tiles)
+  // RTM_STEP_KERNEL picks the context's default propagation kernel: 1 the
+  // single-step kernel, 2 (default) the two-step kernel with one tile per
+  // block (RTM_L2_AHEAD=1 turns on its L2 prefetch of later tiles), 3 the
+  // persistent two-step kernel (RTM_TILE_Z=16 for 16-row tiles), 4 the
+  // two-step kernel with v^{n+1} over v^n (RTM_TILE_Z=32 for 32-row tiles)
   const char *sk = std::getenv("RTM_STEP_KERNEL");
-  ctx->defaults.step_kernel = (sk && sk[0] == '1') ? 1 : ((sk && sk[0] == '2') ? 2 : 3);
+  const int k = sk ? std::atoi(sk) : 0;
+  ctx->defaults.step_kernel = (k >= 1 && k <= 4) ? k : 2;
   const char *tz = std::getenv("RTM_TILE_Z");
-  ctx->defaults.tile_z = (tz && std::atoi(tz) == 16 && ctx->defaults.step_kernel == 3) ? 16 : 24;
+  const int z = tz ? std::atoi(tz) : 24;
+  ctx->defaults.tile_z = ((z == 16 && k == 3) || (z == 32 && k == 4)) ? z : 24;
+  const char *la = std::getenv("RTM_L2_AHEAD");
+  ctx->defaults.l2_ahead = (la && la[0] == '1') ? 1 : 0;
   // RTM_GRAPHS=1 captures each phase of a batch in a CUDA graph by default
   const char *gr = std::getenv("RTM_GRAPHS");
   ctx->defaults.graph = (gr && gr[0] == '1') ? 1 : 0;
@@ -1308,20 +1325,24 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
   int best = -1;
   double best_t = 1e300;
   std::vector<RunConfig> cand;
-  // (kernel, tile height): persistent 24 and 16 rows, one tile per block, single step
-  const int kinds[4][2] = {{3, 24}, {3, 16}, {2, 24}, {1, 24}};
+  // (kernel, tile height, L2 prefetch of later tiles): one tile per block
+  // without and with the prefetch, one tile per block with v^{n+1} over v^n
+  // (24 and 32 rows), persistent (24 and 16 rows), single step
+  const int kinds[7][3] = {{2, 24, 0}, {2, 24, 1}, {4, 24, 0}, {4, 32, 0},
+                           {3, 24, 0}, {3, 16, 0}, {1, 24, 0}};
   for (const auto &kd : kinds)
     for (int graph : {0, 1})
       for (long long items : {bmax, (bmax + 1) / 2}) {
         RunConfig c;
         c.step_kernel = kd[0];
         c.tile_z = kd[1];
+        c.l2_ahead = kd[2];
         c.graph = graph;
         c.max_items = items >= nitems ? 0 : (int)items;
         bool dup = false;
         for (auto &o : cand)
-          dup |= o.step_kernel == c.step_kernel && o.tile_z == c.tile_z && o.graph == c.graph &&
-                 o.max_items == c.max_items;
+          dup |= o.step_kernel == c.step_kernel && o.tile_z == c.tile_z &&
+                 o.l2_ahead == c.l2_ahead && o.graph == c.graph && o.max_items == c.max_items;
         if (!dup) cand.push_back(c);
       }
   rc = RTM_OK;
@@ -1395,6 +1416,7 @@ int rtm_autotune(rtm_ctx *ctx, const rtm_grid *grid, const rtm_acq *acq, const r
     choice[1] = cand[best].max_items;
     choice[2] = cand[best].graph;
     choice[3] = cand[best].tile_z;
+    choice[4] = cand[best].l2_ahead;
   }
   return RTM_OK;
 }

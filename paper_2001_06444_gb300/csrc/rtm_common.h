@@ -66,9 +66,11 @@ struct Geo {
 };
 
 struct Coef {
-  float c0;     // a0 (1/dx^2 + 1/dz^2) (the kernels use the difference form instead)
+  float c0;     // a0 (1/dx^2 + 1/dz^2) (the kernels subtract the centre per ring instead)
   float ax[4];  // a_m / dx^2
   float az[4];  // a_m / dz^2
+  int iso;      // dx == dz: both directions' neighbours are summed before the centre is
+                // subtracted (one ring of 4 neighbours per m), else each direction alone
 };
 
 // Arguments of one batched launch over B items (blockIdx.z = item slot).
@@ -124,6 +126,8 @@ struct Step2Args {
   int one_sample;                // every item uses sample 0 (no lookup before the copies)
   float *v_out;                  // [B][plane] receives v^{n+2}
   float *d_out;                  // [B][plane] receives d^{n+2}
+  const float *v_in, *d_in;      // [B][plane] v^n, d^n (read through the tensor maps; the
+                                 // one-tile-per-block kernel prefetches from them into L2)
   const int *src_row, *src_col;
   const float *wav;
   float src_scale;
@@ -155,7 +159,10 @@ struct Step2RT {
                        // inject c m S from this snapshot at substep 1
   int img_out_idx;     // image with the output field (backward); Born: at substep 2
   int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
-  int reverse;         // persistent kernel: walk the tile list from its end
+  int reverse;         // walk the tile list from its end (snake order over launches)
+  int ahead;           // one-tile-per-block kernel: blocks resident at once (each block
+                       // prefetches into L2 the tile of the block `ahead` launches later);
+                       // 0 = no prefetch
 };
 
 enum { MODE_FWD = 0, MODE_MODEL = 1, MODE_BWD = 2, MODE_BORN = 3 };

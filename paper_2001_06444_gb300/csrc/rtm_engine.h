@@ -21,11 +21,14 @@ struct rtm_server;
 namespace rtm {
 // How a migration is launched (all choices give bit-identical results).
 struct RunConfig {
-  int step_kernel = 3;  // 3: persistent two-step kernel with a copy ring where possible;
-                        // 2: two-step kernel, one tile per block; 1: single-step only
+  int step_kernel = 2;  // 2: two-step kernel, one tile per block, where possible;
+                        // 3: persistent two-step kernel with a copy ring;
+                        // 4: two-step kernel, one tile per block, v^{n+1} over v^n;
+                        // 1: single-step only
   int max_items = 0;    // cap on items in flight (0 = memory budget)
   int graph = 0;        // 1: capture each phase of a batch in a CUDA graph
-  int tile_z = 24;      // centre rows of a two-step tile (16 only with step_kernel 3)
+  int tile_z = 24;      // centre rows of a two-step tile (16 with kernel 3, 32 with kernel 4)
+  int l2_ahead = 0;     // step_kernel 2: each block prefetches a later block's tile into L2
 };
 // Shape key of the autotuner cache.
 struct TuneKey {

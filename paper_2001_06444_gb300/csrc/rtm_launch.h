@@ -28,6 +28,12 @@ cudaError_t launch_step2p(int mode, int tile_z, const CUtensorMap &mv, const CUt
                           const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                           cudaStream_t st);
 size_t step2p_smem_bytes(int tile_z);
+// two-step kernel, one tile per block, v^{n+1} written over v^n (rtm_prop2p.cu):
+// tile_z = 24 or 32 centre rows, maps as for launch_step2p
+cudaError_t launch_step2a(int mode, int tile_z, const CUtensorMap &mv, const CUtensorMap &md,
+                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
+                          cudaStream_t st);
+size_t step2a_smem_bytes(int tile_z);
 // bounded-wait self-test: raises *flag after waiting `ns` for bytes that never arrive
 cudaError_t launch_wait_probe(int *flag, unsigned long long ns, cudaStream_t st);
 int step2_tile_x();

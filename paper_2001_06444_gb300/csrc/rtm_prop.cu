@@ -15,6 +15,9 @@
 // scheme in exact arithmetic.  In FP32 it keeps the time difference to full
 // relative precision instead of to eps |v|, which removes the rounding error
 // that the two-level form feeds into its non-decaying mode at every step.
+// L v is summed ring by ring, the centre taken off each ring's neighbour sum
+// with one rounding (see the stencil below), which keeps the cancellation of
+// the plain 17-term sum out of FP32.
 // The same kernel steps the reverse-time (adjoint) field, which obeys the
 // same recurrence with the data injected at the receivers (§3).
 //
@@ -185,14 +188,27 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step(const StepArgs A, cons
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const float ce = v[4 + l];
-      // L v as sum_m a_m [(v_{+m} - v_0) + (v_{-m} - v_0)] / h^2 (the centre
-      // weight is -2 sum a_m exactly): the differences are small and nearly
-      // exact for smooth fields, so FP32 cancellation no longer dominates
+      // L v ring by ring (the centre weight is -2 sum a_m exactly): the
+      // ring's neighbours are summed, then the centre is taken off with one
+      // rounding, so each ring's term is a small second difference and FP32
+      // cancellation stays small.  dx == dz: one ring of 4 neighbours per m,
+      // fma(v0, -4, (x_-m + x_+m) + (z_-m + z_+m)); otherwise each direction
+      // with its own weight, fma(v0, -2, x_-m + x_+m).
       float lap = 0.f;
+      if (A.k.iso) {
 #pragma unroll
-      for (int m = 4; m >= 1; --m) {
-        lap = fmaf(A.k.ax[m - 1], (v[4 + l - m] - ce) + (v[4 + l + m] - ce), lap);
-        lap = fmaf(A.k.az[m - 1], (lane4(zc[r + 4 - m], l) - ce) + (lane4(zc[r + 4 + m], l) - ce), lap);
+        for (int m = 4; m >= 1; --m) {
+          const float s = (v[4 + l - m] + v[4 + l + m]) +
+                          (lane4(zc[r + 4 - m], l) + lane4(zc[r + 4 + m], l));
+          lap = fmaf(A.k.ax[m - 1], fmaf(ce, -4.f, s), lap);
+        }
+      } else {
+#pragma unroll
+        for (int m = 4; m >= 1; --m) {
+          lap = fmaf(A.k.ax[m - 1], fmaf(ce, -2.f, v[4 + l - m] + v[4 + l + m]), lap);
+          lap = fmaf(A.k.az[m - 1],
+                     fmaf(ce, -2.f, lane4(zc[r + 4 - m], l) + lane4(zc[r + 4 + m], l)), lap);
+        }
       }
       const float c = lane4(cv[r], l), p = lane4(pv[r], l);
       float nd;  // d^{n+1} before injection

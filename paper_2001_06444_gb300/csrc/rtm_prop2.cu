@@ -67,7 +67,7 @@ static_assert(sizeof(float) * EX * EZ % 128 == 0, "tile offsets must stay 128-by
 
 // Substep 1: (v^{n+1}, d^{n+1}) on the extended region, rows 4ty..4ty+3 and
 // columns 4tx..4tx+3 of it, into S.d and S.v1.
-template <int MODE, bool SPONGE>
+template <int MODE, bool SPONGE, bool ISO>
 __device__ __forceinline__ void substep1(Smem &S, const Step2Args &A, const Step2RT &rt, int b,
                                          int x0, int z0) {
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void substep1(Smem &S, const Step2Args &A, const Step
     const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 * tx]);
     const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
     const float gzr = SPONGE ? S.gzs[er] : 1.f;
-    const float4 nd = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    const float4 nd = update4<SPONGE, ISO>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
     *reinterpret_cast<float4 *>(&S.d[er][4 * tx]) = nd;
     if (MODE != MODE_BORN) {
       const float4 ce = zc[r + 4];
@@ -114,7 +114,7 @@ __device__ __forceinline__ void substep1(Smem &S, const Step2Args &A, const Step
 
 // Substep 2: d^{n+2} (res, before injection) and v^{n+1} (cen) on the
 // centre, rows 3ty..3ty+2 and columns 4tx..4tx+3 of it.
-template <int MODE, bool SPONGE>
+template <int MODE, bool SPONGE, bool ISO>
 __device__ __forceinline__ void substep2(const Smem &S, const Step2Args &A, const Step2RT &rt,
                                          int b, int x0, int z0, float4 (&res)[3],
                                          float4 (&cen)[3]) {
@@ -134,7 +134,7 @@ __device__ __forceinline__ void substep2(const Smem &S, const Step2Args &A, cons
     const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 + 4 * tx]);
     const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 + 4 * tx]);
     const float gzr = SPONGE ? S.gzs[er] : 1.f;
-    res[r] = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    res[r] = update4<SPONGE, ISO>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
     cen[r] = zc[r + 4];
   }
   if (MODE == MODE_BORN) {  // as in substep 1
@@ -156,9 +156,13 @@ __global__ void __launch_bounds__(NTH, 3)
   // TMA destinations must be 128-byte aligned: align the base explicitly
   Smem &S = *reinterpret_cast<Smem *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int b = blockIdx.z;
   const Geo &g = A.g;
-  const int x0 = blockIdx.x * C2X, z0 = blockIdx.y * C2Z;
+  // snake order: with `reverse` the launch walks the tiles from the end
+  const bool rev = rt.reverse != 0;
+  const int bx = rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int by = rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+  const int b = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+  const int x0 = bx * C2X, z0 = by * C2Z;
   const int smp = A.one_sample ? 0 : A.item_sample[b];  // c tile's sample, before the copies
   const int shot = A.item_shot[b];
 #ifdef RTM_DEBUG
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(NTH, 3)
   // plane outside the c map, so a bad sample is recorded, not read)
   const bool shot_ok = RTM_IN(b, A.len.items, A.err) && RTM_IN(smp, A.len.nsample, A.err) &&
                        RTM_IN(shot, A.len.nshot, A.err) &&
-                       RTM_IN(blockIdx.y * g.ntx2 + blockIdx.x + 1, g.ntx2 * g.ntz2 + 1, A.err);
+                       RTM_IN(by * g.ntx2 + bx + 1, g.ntx2 * g.ntz2 + 1, A.err);
 #else
   constexpr bool shot_ok = true;
 #endif
@@ -189,6 +193,36 @@ __global__ void __launch_bounds__(NTH, 3)
     tma_load_3d(&S.v0[0][0], &map_v, x0 - 8, z0 - 8, b, &S.bar);
     tma_load_3d(&S.d[0][0], &map_d, x0 - 4, z0 - 4, b, &S.bar);
     tma_load_3d(&S.c[0][0], &map_c, x0 - 4, z0 - 4, smp, &S.bar);
+  }
+  // L2 prefetch of the v and d rows of the tile that the block `ahead`
+  // launches later will load (it takes this block's place on the SM when a
+  // resident block retires), one bulk prefetch per row, clipped to the plane
+  if (rt.ahead > 0 && tid < VZ + EZ) {
+    const long long nblk = (long long)gridDim.x * gridDim.y * gridDim.z;
+    const long long lin =
+        blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z) +
+        rt.ahead;
+    if (lin < nblk) {
+      int px = (int)(lin % gridDim.x);
+      const long long q = lin / gridDim.x;
+      int py = (int)(q % gridDim.y), pz = (int)(q / gridDim.y);
+      if (rev) {
+        px = gridDim.x - 1 - px;
+        py = gridDim.y - 1 - py;
+        pz = gridDim.z - 1 - pz;
+      }
+      const bool vrow = tid < VZ;
+      const int row = vrow ? py * C2Z - 8 + tid : py * C2Z - 4 + (tid - VZ);
+      const int c0 = max(px * C2X - (vrow ? 8 : 4), 0);
+      const int c1 = min(px * C2X - (vrow ? 8 : 4) + (vrow ? VX : EX), g.P);
+      if (row >= 0 && row < g.NZ && c1 > c0) {
+        const float *src = (vrow ? A.v_in : A.d_in) + (long long)pz * g.plane +
+                           (long long)row * g.P + c0;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src),
+                     "r"((unsigned)(c1 - c0) * 4u)
+                     : "memory");
+      }
+    }
   }
   if (!interior) {  // the extended region's sponge factors, edge-clamped
     if (tid < EX) S.gxs[tid] = A.gx[min(max(x0 - 4 + tid, 0), g.P - 1)];
@@ -260,17 +294,24 @@ __global__ void __launch_bounds__(NTH, 3)
   // (blocks clear of the sponge run a body without the sponge formula; a
   // warp whose rows lie 4 or more past the grid skips: substep 2 reads rows
   // up to 4 past its own, and computes none below the grid's last row + 1)
-  if (interior)
-    substep1<MODE, false>(S, A, rt, b, x0, z0);
-  else if (z0 - 4 + 4 * ty < g.NZ + 4)
-    substep1<MODE, true>(S, A, rt, b, x0, z0);
+  if (A.k.iso) {
+    if (interior)
+      substep1<MODE, false, true>(S, A, rt, b, x0, z0);
+    else if (z0 - 4 + 4 * ty < g.NZ + 4)
+      substep1<MODE, true, true>(S, A, rt, b, x0, z0);
+  } else {
+    if (interior)
+      substep1<MODE, false, false>(S, A, rt, b, x0, z0);
+    else if (z0 - 4 + 4 * ty < g.NZ + 4)
+      substep1<MODE, true, false>(S, A, rt, b, x0, z0);
+  }
   __syncthreads();
 
   // injection at step t1 into every cell of the extended region: add to
   // d^{n+1}, then re-form v^{n+1} = v^n + d^{n+1} at those cells (the same
   // rounding order as the single-step kernel)
   {
-    const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
+    const int tile = by * g.ntx2 + bx;
     if (MODE == MODE_FWD || MODE == MODE_MODEL) {
       const int sr = A.src_row[shot] - (z0 - 4), sc = A.src_col[shot] - (x0 - 4);
       if (sr >= 0 && sr < EZ && sc >= 0 && sc < EX) {  // block-uniform
@@ -307,7 +348,7 @@ __global__ void __launch_bounds__(NTH, 3)
 
   // step-(n+1) work on the centre: recording, FP32 snapshot, imaging
   if (MODE == MODE_MODEL || MODE == MODE_BORN) {
-    const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
+    const int tile = by * g.ntx2 + bx;
     const int p0 = shot_ok ? A.rcen_ptr[tile] : 0, p1 = shot_ok ? A.rcen_ptr[tile + 1] : 0;
     const long long r0 = ((long long)b * A.nt + rt.t1) * A.nrec;
     float *ro = A.rec_out + r0;
@@ -374,9 +415,15 @@ __global__ void __launch_bounds__(NTH, 3)
   float4 cen[3];
   if (wide) {
     if (interior) {
-      substep2<MODE, false>(S, A, rt, b, x0, z0, res, cen);
+      if (A.k.iso)
+        substep2<MODE, false, true>(S, A, rt, b, x0, z0, res, cen);
+      else
+        substep2<MODE, false, false>(S, A, rt, b, x0, z0, res, cen);
     } else if (z0 + 3 * ty < g.NZ) {
-      substep2<MODE, true>(S, A, rt, b, x0, z0, res, cen);
+      if (A.k.iso)
+        substep2<MODE, true, true>(S, A, rt, b, x0, z0, res, cen);
+      else
+        substep2<MODE, true, false>(S, A, rt, b, x0, z0, res, cen);
     } else {  // rows past the grid: nothing of them is stored
 #pragma unroll
       for (int r = 0; r < 3; ++r) res[r] = cen[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -385,7 +432,7 @@ __global__ void __launch_bounds__(NTH, 3)
 
   // injection at step t2 on the centre (staged through the d tile)
   {
-    const int tile = blockIdx.y * g.ntx2 + blockIdx.x;
+    const int tile = by * g.ntx2 + bx;
     bool stage = false;
     int sr = -1, sc = -1, p0 = 0, p1 = 0;
     if (MODE == MODE_FWD || MODE == MODE_MODEL) {
@@ -549,19 +596,32 @@ int step2_ext() { return 4; }
 cudaError_t launch_step2(int mode, const CUtensorMap &mv, const CUtensorMap &md,
                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
                          cudaStream_t st) {
-  // the shared-memory opt-in, once per mode (launches come from several
-  // request threads; setting it twice is harmless, the flags are atomic)
-  static std::atomic<bool> attr_set[4];
+  // per (mode, device): the shared-memory opt-in and the number of blocks
+  // resident at once (launches come from several request threads; computing
+  // either twice is harmless)
+  static std::atomic<int> resident[4][64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const size_t smem = step2_smem_bytes();
   dim3 grid(A.g.ntx2, A.g.ntz2, B), block(32, NTH / 32);
   auto launch = [&](auto kernel, int slot) -> cudaError_t {
-    if (!attr_set[slot].load(std::memory_order_acquire)) {
-      const cudaError_t e =
-          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_set[slot].store(true, std::memory_order_release);
+    int nres = resident[slot][dev].load(std::memory_order_acquire);
+    if (nres == 0) {
+      cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (r != cudaSuccess) return r;
+      int per_sm = 0, nsm = 0;
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NTH, smem);
+      if (r != cudaSuccess) return r;
+      r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (r != cudaSuccess) return r;
+      nres = per_sm > 0 ? per_sm * nsm : 1;
+      resident[slot][dev].store(nres, std::memory_order_release);
     }
-    kernel<<<grid, block, smem, st>>>(mv, md, mc, A, rt);
+    Step2RT r2 = rt;
+    r2.ahead = rt.ahead ? nres : 0;  // the block that takes this block's place
+    kernel<<<grid, block, smem, st>>>(mv, md, mc, A, r2);
     return cudaGetLastError();
   };
   switch (mode) {

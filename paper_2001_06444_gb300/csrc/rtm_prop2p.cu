@@ -62,7 +62,7 @@ struct Stage {
   float d[Shape<R1>::EZ][EX];   // d^n -> d^{n+1} -> d^{n+2}, updated in place
   float c[Shape<R1>::EZ][EX];   // (v dt)^2
   float gxs[EX];                // sponge factors of the extended region's columns ...
-  float gzs[32];                // ... and rows (filled for tiles that reach the sponge)
+  float gzs[(Shape<R1>::EZ + 31) / 32 * 32];  // ... and rows (tiles that reach the sponge)
 };
 
 template <int R1>
@@ -71,7 +71,8 @@ struct SmemP {
   unsigned long long bar[2];
   float red[NTH / 32];
 };
-static_assert(sizeof(Stage<4>) % 128 == 0 && sizeof(Stage<3>) % 128 == 0,
+static_assert(sizeof(Stage<4>) % 128 == 0 && sizeof(Stage<3>) % 128 == 0 &&
+                  sizeof(Stage<5>) % 128 == 0,
               "stages must keep the TMA destinations 128-byte aligned");
 static_assert(sizeof(float) * VX * Shape<4>::VZ % 128 == 0 &&
                   sizeof(float) * VX * Shape<3>::VZ % 128 == 0 &&
@@ -164,7 +165,7 @@ __device__ __forceinline__ void prefetch_imaging(const Step2Args &A, const Step2
 // Substep 1 on rows R1 ty .. R1 ty + R1 - 1, columns 4tx..4tx+3 of the
 // extended region: d^{n+1} into nd (Born source included) and S.d; v^n of the
 // same cells into ce.
-template <int MODE, bool SPONGE, int R1>
+template <int MODE, bool SPONGE, bool ISO, int R1>
 __device__ __forceinline__ void substep1p(Stage<R1> &S, const Step2Args &A, const Step2RT &rt,
                                           int b, int x0, int z0, float4 (&ce)[R1],
                                           float4 (&nd)[R1]) {
@@ -183,7 +184,7 @@ __device__ __forceinline__ void substep1p(Stage<R1> &S, const Step2Args &A, cons
     const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 * tx]);
     const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 * tx]);
     const float gzr = SPONGE ? S.gzs[er] : 1.f;
-    nd[r] = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    nd[r] = update4<SPONGE, ISO>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
     ce[r] = zc[r + 4];
   }
   if (MODE == MODE_BORN) {  // the Born source joins each row's new difference
@@ -201,7 +202,7 @@ __device__ __forceinline__ void substep1p(Stage<R1> &S, const Step2Args &A, cons
 
 // Substep 2 on centre rows R2 ty .. R2 ty + R2 - 1: d^{n+2} (res, before
 // injection) and v^{n+1} (cen), reading v^{n+1} from the v^n tile's offset.
-template <int MODE, bool SPONGE, int R1>
+template <int MODE, bool SPONGE, bool ISO, int R1>
 __device__ __forceinline__ void substep2p(const Stage<R1> &S, const Step2Args &A,
                                           const Step2RT &rt, int b, int x0, int z0,
                                           float4 (&res)[R1 - 1], float4 (&cen)[R1 - 1]) {
@@ -221,7 +222,7 @@ __device__ __forceinline__ void substep2p(const Stage<R1> &S, const Step2Args &A
     const float4 dv = *reinterpret_cast<const float4 *>(&S.d[er][4 + 4 * tx]);
     const float4 cv = *reinterpret_cast<const float4 *>(&S.c[er][4 + 4 * tx]);
     const float gzr = SPONGE ? S.gzs[er] : 1.f;
-    res[r] = update4<SPONGE>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
+    res[r] = update4<SPONGE, ISO>(&zc[r], xl, xr, dv, cv, A.k, gzr, gxs);
     cen[r] = zc[r + 4];
   }
   if (MODE == MODE_BORN) {
@@ -319,10 +320,17 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
   float4 ce[R1], nd[R1];
   const bool run1 = interior || (z0 - 4 + R1 * ty < g.NZ + 4);  // warp-uniform
   if (run1) {
-    if (interior)
-      substep1p<MODE, false, R1>(S, A, rt, b, x0, z0, ce, nd);
-    else
-      substep1p<MODE, true, R1>(S, A, rt, b, x0, z0, ce, nd);
+    if (A.k.iso) {
+      if (interior)
+        substep1p<MODE, false, true, R1>(S, A, rt, b, x0, z0, ce, nd);
+      else
+        substep1p<MODE, true, true, R1>(S, A, rt, b, x0, z0, ce, nd);
+    } else {
+      if (interior)
+        substep1p<MODE, false, false, R1>(S, A, rt, b, x0, z0, ce, nd);
+      else
+        substep1p<MODE, true, false, R1>(S, A, rt, b, x0, z0, ce, nd);
+    }
   }
   __syncthreads();  // every read of v^n is done: the tile may take v^{n+1}
 
@@ -405,9 +413,15 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
   float4 cen[R2];
   if (wide) {
     if (interior) {
-      substep2p<MODE, false, R1>(S, A, rt, b, x0, z0, res, cen);
+      if (A.k.iso)
+        substep2p<MODE, false, true, R1>(S, A, rt, b, x0, z0, res, cen);
+      else
+        substep2p<MODE, false, false, R1>(S, A, rt, b, x0, z0, res, cen);
     } else if (z0 + R2 * ty < g.NZ) {
-      substep2p<MODE, true, R1>(S, A, rt, b, x0, z0, res, cen);
+      if (A.k.iso)
+        substep2p<MODE, true, true, R1>(S, A, rt, b, x0, z0, res, cen);
+      else
+        substep2p<MODE, true, false, R1>(S, A, rt, b, x0, z0, res, cen);
     } else {  // rows past the grid: nothing of them is stored
 #pragma unroll
       for (int r = 0; r < R2; ++r) res[r] = cen[r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -566,8 +580,81 @@ __global__ void __launch_bounds__(NTH, 2)
   }
 }
 
+// One tile per block with the same tile body and a single stage: 3 blocks per
+// SM overlap one another's copies.  Writing v^{n+1} over v^n frees the
+// separate v^{n+1} array of k_step2, which makes room for 120 x 32 tiles
+// (R1 = 5, 67 KB) at 3 blocks per SM.  Snake order as in k_step2p.
+template <int R1>
+struct Smem1 {
+  Stage<R1> st;
+  unsigned long long bar;
+  float red[NTH / 32];
+};
+
+template <int MODE, int R1>
+__global__ void __launch_bounds__(NTH, 3)
+    k_step2a(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_d,
+             const __grid_constant__ CUtensorMap map_c, const Step2Args A, const Step2RT rt,
+             int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem1<R1> &S =
+      *reinterpret_cast<Smem1<R1> *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if ((int)blockIdx.x >= ntiles) return;  // (the grid is sized to the tiles)
+  const int t = rt.reverse ? ntiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.bar)), "r"(1)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  issue_tile<R1>(S.st, &S.bar, &map_v, &map_d, &map_c, A, t);
+  if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0))
+    prefetch_imaging<R1>(A, rt, t);
+  const bool ok = mbar_wait_bounded(&S.bar, 0, kWaitNs);
+  if (__syncthreads_or(!ok)) {  // (block-wide; also orders the staged sponge factors)
+    if (tid == 0) atomicExch(A.err, 1);
+    mbar_wait_bounded(&S.bar, 0, kWaitNs);  // let the copies in flight land (bounded)
+    return;
+  }
+  tile_body<MODE, R1>(S.st, S.red, A, rt, t);
+}
+
 size_t step2p_smem_bytes(int tile_z) {
   return (tile_z == 16 ? sizeof(SmemP<3>) : sizeof(SmemP<4>)) + 128;
+}
+
+size_t step2a_smem_bytes(int tile_z) {
+  return (tile_z == 32 ? sizeof(Smem1<5>) : sizeof(Smem1<4>)) + 128;
+}
+
+cudaError_t launch_step2a(int mode, int tile_z, const CUtensorMap &mv, const CUtensorMap &md,
+                          const CUtensorMap &mc, const Step2Args &A, const Step2RT &rt, int B,
+                          cudaStream_t st) {
+  if (tile_z != 24 && tile_z != 32) return cudaErrorInvalidValue;
+  const long long ntl = (long long)B * A.g.ntx2 * A.g.ntz2;
+  if (ntl < 1 || ntl > 0x7fffffffLL) return cudaErrorInvalidValue;
+  static std::atomic<bool> attr_set[8];
+  const size_t smem = step2a_smem_bytes(tile_z);
+  dim3 block(32, NTH / 32);
+  auto launch = [&](auto kernel, int slot) -> cudaError_t {
+    if (!attr_set[slot].load(std::memory_order_acquire)) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set[slot].store(true, std::memory_order_release);
+    }
+    kernel<<<(unsigned)ntl, block, smem, st>>>(mv, md, mc, A, rt, (int)ntl);
+    return cudaGetLastError();
+  };
+  const int h = tile_z == 32 ? 4 : 0;
+  switch (mode) {
+    case MODE_FWD: return h ? launch(k_step2a<MODE_FWD, 5>, 4) : launch(k_step2a<MODE_FWD, 4>, 0);
+    case MODE_MODEL: return h ? launch(k_step2a<MODE_MODEL, 5>, 5) : launch(k_step2a<MODE_MODEL, 4>, 1);
+    case MODE_BWD: return h ? launch(k_step2a<MODE_BWD, 5>, 6) : launch(k_step2a<MODE_BWD, 4>, 2);
+    case MODE_BORN: return h ? launch(k_step2a<MODE_BORN, 5>, 7) : launch(k_step2a<MODE_BORN, 4>, 3);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step2p(int mode, int tile_z, const CUtensorMap &mv, const CUtensorMap &md,

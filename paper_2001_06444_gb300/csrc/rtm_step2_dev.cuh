@@ -136,14 +136,11 @@ __device__ __forceinline__ void block_max_atomic(float v, unsigned *dst, float *
   }
 }
 
-// Paired FP32 arithmetic (two lanes per instruction).  Each lane rounds
-// exactly like the scalar operation, so results equal the scalar kernel's;
-// a - b is formed as fma(b, -1, a), which rounds once like a subtraction.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
+// Paired FP32 arithmetic (__fadd2_rn, __ffma2_rn, __fmul2_rn: two lanes per
+// instruction).  Each lane rounds exactly like the scalar operation, so
+// results equal the scalar kernel's.
 
-// One leapfrog update of 4 consecutive points in difference form.
+// One leapfrog update of 4 consecutive points.
 //   zc[0..8]: the 9 rows (centre row zc[4]) of the 4-column strip,
 //   xl, xr:   the 4 columns left and right of the strip in the centre row,
 //   dv, cv:   d^n and c at the strip,
@@ -153,9 +150,18 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 //             shared memory).  Blocks clear of the sponge compile in the
 //             interior formula alone.  (Choosing between the two forms per
 //             row measured slower.)
+//   ISO:      dx == dz.  The Laplacian is summed ring by ring, m = 4..1: the
+//             ring's neighbours are added first, then the centre is taken
+//             off with one rounding, t_m = fma(v0, -4, (v_-m + v_+m) +
+//             (w_-m + w_+m)) along x (v) and z (w), lap = fma(a_m/h^2, t_m,
+//             lap).  Otherwise each direction alone, fma(v0, -2, v_-m +
+//             v_+m) scaled by its own a_m/dx^2 or a_m/dz^2.  Taking the
+//             centre off per ring keeps FP32 cancellation small (the
+//             17-term sum of the plain form does not).
 // Returns d^{n+1} (before injection); v^{n+1} = v^n + d^{n+1}.  Lanes are
-// processed in pairs (0,1) and (2,3).
-template <bool SPONGE>
+// processed in pairs (0,1) and (2,3); each lane rounds as the scalar form of
+// the single-step kernel.
+template <bool SPONGE, bool ISO>
 __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, const float4 &xr,
                                           const float4 &dv, const float4 &cv, const Coef &k,
                                           float gzr, const float *gxs) {
@@ -170,14 +176,20 @@ __device__ __forceinline__ float4 update4(const float4 *zc, const float4 &xl, co
     for (int m = 4; m >= 1; --m) {
       const float2 xm = make_float2(v[4 + l - m], v[5 + l - m]);
       const float2 xp = make_float2(v[4 + l + m], v[5 + l + m]);
-      const float2 tx = __fadd2_rn(sub2(xm, ce), sub2(xp, ce));
-      lap = __ffma2_rn(make_float2(k.ax[m - 1], k.ax[m - 1]), tx, lap);
       const float2 zm = l == 0 ? make_float2(zc[4 - m].x, zc[4 - m].y)
                                : make_float2(zc[4 - m].z, zc[4 - m].w);
       const float2 zp = l == 0 ? make_float2(zc[4 + m].x, zc[4 + m].y)
                                : make_float2(zc[4 + m].z, zc[4 + m].w);
-      const float2 tz = __fadd2_rn(sub2(zm, ce), sub2(zp, ce));
-      lap = __ffma2_rn(make_float2(k.az[m - 1], k.az[m - 1]), tz, lap);
+      if (ISO) {
+        const float2 s = __fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(zm, zp));
+        const float2 t = __ffma2_rn(ce, make_float2(-4.f, -4.f), s);
+        lap = __ffma2_rn(make_float2(k.ax[m - 1], k.ax[m - 1]), t, lap);
+      } else {
+        const float2 tx = __ffma2_rn(ce, make_float2(-2.f, -2.f), __fadd2_rn(xm, xp));
+        lap = __ffma2_rn(make_float2(k.ax[m - 1], k.ax[m - 1]), tx, lap);
+        const float2 tz = __ffma2_rn(ce, make_float2(-2.f, -2.f), __fadd2_rn(zm, zp));
+        lap = __ffma2_rn(make_float2(k.az[m - 1], k.az[m - 1]), tz, lap);
+      }
     }
     const float2 c = l == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w);
     const float2 p = l == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);

@@ -262,10 +262,11 @@ class Context:
     def autotune(self, grid: Grid, acq: Acq, opts: Opts, trial_steps: int = 64) -> dict:
         """Time the launch configurations on short synthetic trials and keep
         the fastest for this shape; returns it."""
-        ch = (C.c_int * 4)()
+        ch = (C.c_int * 5)()
         self._check(lib().rtm_autotune(self.h, C.byref(grid), C.byref(acq), C.byref(opts),
                                        int(trial_steps), ch, C.c_void_p(0)))
-        return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2], "tile_z": ch[3]}
+        return {"step_kernel": ch[0], "max_items": ch[1], "graph": ch[2], "tile_z": ch[3],
+                "l2_ahead": ch[4]}
 
     def inject_wait_timeout(self, count: int = 1):
         """The next `count` migration or modelling calls start with their

@@ -46,9 +46,11 @@ def test_autotune_and_graph_capture_are_bitwise_neutral(dtype):
     with rtm.Context(0) as ctx:
         base = _migrate(ctx, s, v, seis, opts)
         choice = ctx.autotune(rtm.make_grid(*s.grid_tuple()), acq, opts, trial_steps=40)
-        assert choice["step_kernel"] in (1, 2, 3) and choice["graph"] in (0, 1)
-        assert choice["tile_z"] in (16, 24) and (choice["tile_z"] == 24 or
-                                                 choice["step_kernel"] == 3)
+        assert choice["step_kernel"] in (1, 2, 3, 4) and choice["graph"] in (0, 1)
+        assert choice["tile_z"] in (16, 24, 32)
+        assert choice["tile_z"] == 24 or (choice["step_kernel"], choice["tile_z"]) in ((3, 16),
+                                                                                      (4, 32))
+        assert choice["l2_ahead"] in (0, 1)
         assert choice["max_items"] >= 0
         assert np.array_equal(_migrate(ctx, s, v, seis, opts), base)
         assert np.array_equal(_migrate(ctx, s, v, seis, opts, side), base)
