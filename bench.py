@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--iters", type=int, default=2, help="lsrtm: CGLS iterations per step")
     p.add_argument("--serve-snap", default="f16", choices=["f16", "bf16"],
                    help="serve: snapshot format of the batched, served form")
+    p.add_argument("--serve-plain", type=int, default=1, choices=[0, 1],
+                   help="serve: also time the plain form (0 skips it; no batched/plain ratio)")
     return p.parse_args()
 
 
@@ -102,24 +104,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per point update of the step kernels from the committed ncu
-    summary, if it was taken on the current kernel sources; else None."""
+def step_sources_digest():
+    """Hash of the propagation kernels' sources (the ncu summaries record it)."""
     import hashlib
 
     h = hashlib.sha256()
     for f in ("rtm_prop.cu", "rtm_prop2.cu", "rtm_prop2p.cu", "rtm_step2_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2001_06444_gb300", "csrc", f), "rb").read())
-    digest = h.hexdigest()[:16]
-    summ = os.path.join(ROOT, "profiles", "k_step2_small.md")
-    try:
-        for line in open(summ):
-            if line.startswith("traffic_bytes_per_update:"):
-                parts = line.split()
-                if len(parts) >= 4 and parts[3] == digest:
-                    return float(parts[1])
-    except OSError:
-        pass
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per point update of step kernel `kernel` (e.g. "k_step2a")
+    from the committed ncu summaries under profiles/, if one was taken on the
+    current kernel sources; else None.  A summary carries the line
+    `traffic_bytes_per_update: <B> <sources digest> <kernel>`."""
+    import glob
+
+    digest = step_sources_digest()
+    for summ in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        try:
+            for line in open(summ):
+                if line.startswith("traffic_bytes_per_update:"):
+                    parts = line.split()
+                    if len(parts) >= 4 and parts[2] == digest and parts[3] == kernel:
+                        return float(parts[1])
+        except OSError:
+            pass
     return None
 
 
@@ -284,7 +295,8 @@ def run_native(args, world, rank, local):
     gpt = stats["point_updates"] * world / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     achieved = stats["step_bytes"] / (stats["step_ms"] / 1e3) / 1e9 if stats["step_ms"] else None
-    per_update = profile_traffic()
+    kname = STEP_KERNEL_NAMES.get(tuned.get("step_kernel"), "k_step").split()[0]
+    per_update = profile_traffic(kname)
     launches_step = stats["step_launches"]
     traffic = None
     if per_update is not None and launches_step:
@@ -396,7 +408,7 @@ def _survey_request(spec, snap, dev):
                 opts=rtm.Opts(4, snap, 1e-6, 1))
 
 
-def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
+def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16", plain=True):
     """Poisson stream of mixed migration requests through rtm_submit/rtm_poll
     (continuous batching, half-precision snapshots: FP16 by default, which
     keeps the served images within 1e-2 of the plain form; BF16 does not on
@@ -423,15 +435,17 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
     total_upd = sum(2.0 * r["s"].nshot * r["s"].nt * (r["s"].nz + 2 * r["s"].nb) *
                     (r["s"].nx + 2 * r["s"].nb) for r in reqs)
     # plain form: one request at a time, one shot in flight, FP32 snapshots
-    ctx.set_batch(1)
-    t = time.perf_counter()
-    for r in reqs:
-        ctx.migrate(r["grid"], r["vm"], r["acq"], r["seis"], rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1),
-                    r["img"])
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t
-    ctx.set_batch(0)
-    plain_img = [r["img"].clone() for r in reqs]
+    plain_s, plain_img = None, None
+    if plain:
+        ctx.set_batch(1)
+        t = time.perf_counter()
+        for r in reqs:
+            ctx.migrate(r["grid"], r["vm"], r["acq"], r["seis"],
+                        rtm.Opts(4, rtm.SNAP_F32, 1e-6, 1), r["img"])
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t
+        ctx.set_batch(0)
+        plain_img = [r["img"].clone() for r in reqs]
 
     def serve(gaps_s):
         """Submit request i after gaps_s[i] seconds; returns (wall, latencies)."""
@@ -465,16 +479,23 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
         failed = sum(1 for v in done.values() if v[0] != rtm.REQ_DONE)
         if errors:
             print(f"serve: {failed} requests failed, first: {errors[0]}", file=sys.stderr)
-        return wall, np.array([done[tk][1] for tk, _ in tickets]), failed
+        subs = np.array([sub - t0 for _, sub in tickets])
+        return wall, np.array([done[tk][1] for tk, _ in tickets]), failed, subs
 
     # batched capacity: every request submitted at once
-    cap_wall, _, cap_failed = serve(np.zeros(len(reqs)))
+    cap_wall, _, cap_failed, _ = serve(np.zeros(len(reqs)))
     capacity = len(reqs) / cap_wall
     rate = rate_arg or 0.8 * capacity
     unit_gaps = np.diff([0.0] + [sp["t"] for sp in specs])  # unit-rate Poisson gaps
-    served_s, lat, failed = serve(unit_gaps / rate)
+    served_s, lat, failed, subs = serve(unit_gaps / rate)
+    # the slowest requests: size, arrival and latency
+    work = [2.0 * sp["nshot"] * sp["nt"] * (sp["nz"] + 40) * (sp["nx"] + 40) for sp in specs]
+    slowest = [{"grid": f'{specs[i]["nx"]}x{specs[i]["nz"]}', "shots": specs[i]["nshot"],
+                "nt": specs[i]["nt"], "gupdates": round(work[i] / 1e9, 1),
+                "arrived_s": round(float(subs[i]), 2), "latency_s": round(float(lat[i]), 2)}
+               for i in np.argsort(-lat)[:8]]
     errs = []
-    for r, p in zip(reqs, plain_img):
+    for r, p in zip(reqs, plain_img or []):
         a, b = r["img"].double(), p.double()
         errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
     line = {
@@ -486,10 +507,12 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
         "served": {"shots_per_s": total_shots / served_s, "wall_s": served_s,
                    "p50_latency_s": float(np.percentile(lat, 50)),
                    "p99_latency_s": float(np.percentile(lat, 99)), "failed": failed},
-        "plain_fp32_one_shot": {"shots_per_s": total_shots / plain_s, "wall_s": plain_s,
-                                "gpt_updates_per_s": total_upd / plain_s / 1e9},
-        "speedup_batched_vs_plain": plain_s / cap_wall,
-        "image_rel_l2_vs_plain_max": max(errs),
+        "slowest_requests": slowest,
+        "plain_fp32_one_shot": ({"shots_per_s": total_shots / plain_s, "wall_s": plain_s,
+                                 "gpt_updates_per_s": total_upd / plain_s / 1e9}
+                                if plain_s else None),
+        "speedup_batched_vs_plain": (plain_s / cap_wall) if plain_s else None,
+        "image_rel_l2_vs_plain_max": max(errs) if errs else None,
         "grids": sorted({(sp["nx"], sp["nz"]) for sp in specs}),
     }
     ctx.close()
@@ -499,7 +522,8 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16"):
 
 
 def run_serve(args, local):
-    print(json.dumps(serve_measurement(local, args.requests, args.rate, args.serve_snap)), flush=True)
+    print(json.dumps(serve_measurement(local, args.requests, args.rate, args.serve_snap,
+                                       plain=bool(args.serve_plain))), flush=True)
 
 
 def run_ensemble(args, world, rank, local):

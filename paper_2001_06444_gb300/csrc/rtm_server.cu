@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -50,6 +52,8 @@ struct rtm_server {
   int running = 0;
   int peak_running = 0;  // most requests running at once
   long long backfilled = 0;  // requests admitted past a waiting head
+  bool log = false;          // RTM_SERVER_LOG=1: admissions and completions to stderr
+  Clock::time_point t0 = Clock::now();
   static constexpr int kMaxQueue = 4096;
   static constexpr int kMaxRunning = 32;
   static constexpr int kMaxOvertake = 16;    // backfill admissions past one waiting head
@@ -95,6 +99,10 @@ static void run_request(rtm_ctx *ctx, rtm_server *S, std::shared_ptr<rtm_req_sta
     q->err = err;
     q->state = rc ? RTM_REQ_FAILED : RTM_REQ_DONE;
     S->running--;
+    if (S->log)
+      std::fprintf(stderr, "rtm-server %.3f done id=%llu rc=%d running=%d\n",
+                   std::chrono::duration<double>(Clock::now() - S->t0).count(),
+                   (unsigned long long)q->id, rc, S->running);
   }
   S->cv.notify_all();
 }
@@ -109,6 +117,13 @@ static void admit(rtm_ctx *ctx, rtm_server *S, const std::shared_ptr<rtm_req_sta
   const long long nitems = q->r.acq.nshot;
   long long B = (long long)((got - q->plan.shared_bytes) / q->plan.item_bytes);
   B = std::max<long long>(1, std::min<long long>(B, nitems));
+  if (S->log)
+    std::fprintf(stderr,
+                 "rtm-server %.3f admit id=%llu grid=%dx%d shots=%d nt=%d B=%lld got=%.2fGB "
+                 "want=%.2fGB running=%d queued=%zu\n",
+                 std::chrono::duration<double>(Clock::now() - S->t0).count(),
+                 (unsigned long long)q->id, q->r.grid.nx, q->r.grid.nz, q->r.acq.nshot,
+                 q->r.grid.nt, B, got / 1e9, q->want / 1e9, S->running, S->queue.size());
   std::thread(run_request, ctx, S, q, (int)B).detach();
   S->cv.notify_all();
 }
@@ -169,6 +184,8 @@ static rtm_server *ensure_server(rtm_ctx *ctx) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!ctx->server) {
     ctx->server = new rtm_server();
+    const char *lg = std::getenv("RTM_SERVER_LOG");
+    ctx->server->log = lg && lg[0] == '1';
     ctx->server->sched = std::thread(scheduler, ctx, ctx->server);
   }
   return ctx->server;
