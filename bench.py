@@ -448,32 +448,42 @@ def serve_measurement(local, nreq, rate_arg=0.0, snap_name="f16", plain=True):
         plain_img = [r["img"].clone() for r in reqs]
 
     def serve(gaps_s):
-        """Submit request i after gaps_s[i] seconds; returns (wall, latencies)."""
+        """Submit request i after gaps_s[i] seconds; returns (wall, latencies).
+        Outstanding requests are polled while later ones wait to be submitted,
+        so a latency ends when its request ends, not when submitting does."""
         for r in reqs:
             r["img"].zero_()
         torch.cuda.synchronize()
         tickets = []
+        done = {}
+        errors = []
+        pending = []
+
+        def sweep():
+            for item in list(pending):
+                tk, sub = item
+                st, _ = ctx.poll(tk, 0)
+                if st in (rtm.REQ_DONE, rtm.REQ_FAILED):
+                    done[tk] = (st, time.perf_counter() - sub)
+                    pending.remove(item)
+                    if st == rtm.REQ_FAILED:
+                        errors.append(ctx.last_error())
+
         t0 = time.perf_counter()
         due = t0
         for r, gap in zip(reqs, gaps_s):
             due += gap
             while time.perf_counter() < due:
+                sweep()
                 time.sleep(0.0002)
             sub = time.perf_counter()
             req = rtm.Request(r["grid"], r["vm"].data_ptr(), r["acq"], r["seis"].data_ptr(),
                               r["opts"], r["img"].data_ptr())
             tickets.append((ctx.submit(req), sub))
-        done = {}
-        errors = []
-        while len(done) < len(tickets):
-            for tk, sub in tickets:
-                if tk in done:
-                    continue
-                st, _ = ctx.poll(tk, 1)
-                if st in (rtm.REQ_DONE, rtm.REQ_FAILED):
-                    done[tk] = (st, time.perf_counter() - sub)
-                    if st == rtm.REQ_FAILED:
-                        errors.append(ctx.last_error())
+            pending.append(tickets[-1])
+        while pending:
+            sweep()
+            time.sleep(0.0002)
         wall = time.perf_counter() - t0
         torch.cuda.synchronize()
         failed = sum(1 for v in done.values() if v[0] != rtm.REQ_DONE)
