@@ -27,6 +27,7 @@
 
 #include "rtm_engine.h"
 #include "rtm_launch.h"
+#include "rtm_trace.h"
 
 namespace rtm {
 
@@ -705,6 +706,7 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
   const int rc = issue();
   cudaGraph_t gph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &gph);
+  trace_mark("  graph captured");
   if (rc) {
     if (gph) cudaGraphDestroy(gph);
     return rc;
@@ -713,9 +715,12 @@ static int run_phase(rtm_ctx *ctx, bool graph, cudaStream_t st, F issue) {
   cudaGraphExec_t ex = nullptr;
   const cudaError_t ei = cudaGraphInstantiate(&ex, gph, 0);
   cudaGraphDestroy(gph);
+  trace_mark("  graph instantiated");
   if (ei != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
   const cudaError_t el = cudaGraphLaunch(ex, st);
+  trace_mark("  graph launched");
   cudaGraphExecDestroy(ex);  // released once the launch completes
+  trace_mark("  graph released");
   if (el != cudaSuccess) return fail(ctx, RTM_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(el));
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -729,10 +734,15 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
                    int B, cudaStream_t st, const RunConfig &cfg, const float *born_refl,
                    float *born_out, LateCopy *late, int flag_slot) {
   Common C;
-  int rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z,
-                        cfg.l2_ahead);
+  int rc;
+  {
+    PhaseRange ph("setup");
+    rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z,
+                      cfg.l2_ahead);
+  }
   if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
+  trace_mark("tables and model set up");
   const Geo &g = C.g;
   const int nsnap = gr.nt / op.isnap;
   const long long nitems = (long long)nsample * acq.nshot;
@@ -937,8 +947,12 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     if (!cpC) {
       // forward with every snapshot S^k, k in K; then backward with imaging
       if ((rc = mark())) return rc;
-      rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, true, false); });
+      {
+        PhaseRange ph("forward");
+        rc = run_phase(ctx, graph, st, [&]() { return fwd_range(F, 0, nt, 0, true, false); });
+      }
       if (rc) return rc;
+      trace_mark("forward phase enqueued");
       if ((rc = mark())) return rc;
       if (born_refl) {
         // Born modelling: the perturbation field starts at rest; each step
@@ -982,8 +996,12 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
       if ((rc = zero_fields(ctx, F, g, nb, st))) return rc;
       if ((rc = issue_late(q0 / B))) return rc;
       if ((rc = mark())) return rc;
-      rc = run_phase(ctx, graph, st, [&]() { return bwd_range(F, nt, 0, 0); });
+      {
+        PhaseRange ph("backward");
+        rc = run_phase(ctx, graph, st, [&]() { return bwd_range(F, nt, 0, 0); });
+      }
       if (rc) return rc;
+      trace_mark("backward phase enqueued");
       if ((rc = mark())) return rc;
     } else {
       // forward keeping the state every cpC steps; then, segment by segment
@@ -1524,6 +1542,7 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
                           const rtm_acq *acq, const float *seis, const rtm_opts *opts,
                           float *images, void *stream, bool raw = false) {
   if (!ctx) return RTM_ERR_ARG;
+  CallTrace trace(raw ? "rtm_migrate_adjoint" : (nsample > 1 ? "rtm_migrate_ensemble" : "rtm_migrate"));
   int rc;
   if ((rc = check_grid(ctx, grid)) || (rc = check_acq(ctx, grid, acq, true)) ||
       (rc = check_opts(ctx, opts)))
@@ -1563,16 +1582,20 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   const int slot = flag_acquire(ctx);
   rc = view_in(ctx, v, vels, vbytes, st);
   if (!rc) rc = check_velocity(ctx, *grid, v.d, (long long)nsample * grid->nx * grid->nz, st);
+  trace_mark("velocity staged and checked");
   // host seismograms: allocate now, upload behind the first forward phase
   if (!rc) rc = view_out(ctx, s, const_cast<float *>(seis), sbytes, st);
   if (!rc && s.staged)
     rc = late_begin(ctx, late, seis, s.d, (size_t)grid->nt * acq->nrec * 4, st);
   if (!rc) rc = view_out(ctx, im, images, vbytes, st);
+  trace_mark("buffers ready");
   if (!rc)
     rc = migrate_device(ctx, *grid, nsample, v.d, *acq, s.d, op, im.d, B, st, cfg, nullptr,
                         nullptr, s.staged ? &late : nullptr, slot);
+  trace_mark("migration enqueued");
   late_end(late);
   if (!rc) rc = view_finish(ctx, im, images, vbytes, st);
+  trace_mark("image returned");
   if (!rc && (im.staged || ctx->prof))
     rc = own_wait_flag(ctx, slot);  // the stream was synchronised
   else
