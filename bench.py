@@ -58,6 +58,8 @@ def parse():
                    help="with --kernel 3 (16, 24) or 4 (24, 32): centre rows of a tile")
     p.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                    help="with --kernel 1-3: capture each phase in a CUDA graph")
+    p.add_argument("--image-input", type=int, default=0, choices=[0, 1],
+                   help="with --kernel 2-4: backward launches image their input field")
     p.add_argument("--l2-ahead", type=int, default=0, choices=[0, 1],
                    help="with --kernel 2: each block prefetches a later block's tile into L2")
     p.add_argument("--snap", default="f32", choices=["f32", "bf16", "f16"])
@@ -253,6 +255,7 @@ def run_native(args, world, rank, local):
         os.environ["RTM_TILE_Z"] = str(args.tile_z)
         os.environ["RTM_GRAPHS"] = str(args.graphs)
         os.environ["RTM_L2_AHEAD"] = str(args.l2_ahead)
+        os.environ["RTM_IMAGE_INPUT"] = str(args.image_input)
     ctx = rtm.Context(local)
     ctx.model(grid, vel_true, acq, -1, seis)  # observed data, untimed
     torch.cuda.synchronize()
@@ -261,7 +264,8 @@ def run_native(args, world, rank, local):
     if args.kernel:
         tuned = {"step_kernel": args.kernel, "max_items": args.batch, "graph": args.graphs,
                  "tile_z": args.tile_z if args.kernel in (3, 4) else 24,
-                 "l2_ahead": args.l2_ahead if args.kernel == 2 else 0, "fixed": True}
+                 "l2_ahead": args.l2_ahead if args.kernel == 2 else 0,
+                 "image_input": args.image_input, "fixed": True}
     else:
         tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
     for _ in range(args.warmup):

@@ -884,6 +884,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
         r.snap_out_idx = (store && !half && inK(n + 2)) ? idx(n + 2) : -1;
         r.max_out_idx = (store && half && inK(n + 2)) ? idx(n + 2) : -1;
         r.img_mid_idx = r.img_out_idx = -1;
+        r.img_in_idx = -1;
         r.dmax_flag = 0;
         if ((r2 = step2(ctx, MODE_FWD, A2, C, Fs, r, nb, st))) return r2;
         stored = !half;
@@ -908,30 +909,55 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
     return RTM_OK;
   };
   // Backward steps k = k1 .. k0+1 on Ws, imaging with slot k/isnap - 1 - kbase.
+  // A two-step launch images its INPUT field where it can (img_in): the loads
+  // of its imaging operands then start before its tile copies land.  With an
+  // even isnap the steps are paired so that the imaging fields are launch
+  // inputs: one single step comes first when k1 is even.  A field is imaged
+  // as an output only when no two-step launch takes it as input.  Every field
+  // is imaged once, in the same order, so images do not change.
   auto bwd_range = [&](Fields &Ws, int k1, int k0, int kbase) -> int {
     int r2;
     auto idx = [&](int k) { return k / isnap - 1 - kbase; };
-    for (int k = k1; k > k0;) {
+    auto single = [&](int k) -> int {  // w^k from w^{k+1}; images w^k
+      StepRT r{};
+      r.n = k;
+      r.snap_idx = r.max_idx = -1;
+      r.img_idx = inK(k) ? idx(k) : -1;
+      r.dmax_flag = (k == isnap) ? 1 : 0;
+      ++step_launches;
+      return step1(ctx, MODE_BWD, A, Ws, r, nb, st);
+    };
+    int k = k1;
+    bool in_done = true;  // the next launch's input needs no imaging here
+    const bool use_in = cfg.image_input != 0;
+    if (use_in && two && isnap % 2 == 0 && k1 % 2 == 0 && k1 - 2 > k0) {
+      if ((r2 = single(k))) return r2;
+      k -= 1;
+    }
+    while (k > k0) {
       if (two && k - 1 > k0) {
         Step2RT r;
         r.t1 = k - 1;
         r.t2 = k - 2;
         r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
+        r.img_in_idx = (!in_done && inK(k + 1)) ? idx(k + 1) : -1;
         r.img_mid_idx = inK(k) ? idx(k) : -1;
-        r.img_out_idx = inK(k - 1) ? idx(k - 1) : -1;
-        r.dmax_flag = (k == isnap) ? 1 : (k - 1 == isnap ? 2 : 0);
+        // the launch at k - 2 takes w^{k-1} as input (and images it there)
+        const bool next_two = use_in && k - 3 > k0;
+        r.img_out_idx = (inK(k - 1) && !next_two) ? idx(k - 1) : -1;
+        r.dmax_flag = (r.img_in_idx >= 0 && k + 1 == isnap)    ? 3
+                      : (r.img_mid_idx >= 0 && k == isnap)     ? 1
+                      : (r.img_out_idx >= 0 && k - 1 == isnap) ? 2
+                                                               : 0;
         if ((r2 = step2(ctx, MODE_BWD, A2, C, Ws, r, nb, st))) return r2;
+        ++step_launches;
+        in_done = !next_two;
         k -= 2;
       } else {
-        StepRT r{};
-        r.n = k;
-        r.snap_idx = r.max_idx = -1;
-        r.img_idx = inK(k) ? idx(k) : -1;
-        r.dmax_flag = (k == isnap) ? 1 : 0;
-        if ((r2 = step1(ctx, MODE_BWD, A, Ws, r, nb, st))) return r2;
+        if ((r2 = single(k))) return r2;
+        in_done = true;
         k -= 1;
       }
-      ++step_launches;
     }
     return RTM_OK;
   };
@@ -973,6 +999,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
               r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
               r.img_mid_idx = slot(n + 1);
               r.img_out_idx = slot(n + 2);
+              r.img_in_idx = -1;
               r.dmax_flag = 0;
               r2 = step2(ctx, MODE_BORN, A2, C, F, r, nb, st);
               n += 2;
@@ -1110,7 +1137,7 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
         r.t1 = n;
         r.t2 = n + 1;
         r.snap_in_idx = r.snap_mid_idx = r.snap_out_idx = r.max_out_idx = -1;
-        r.img_mid_idx = r.img_out_idx = -1;
+        r.img_mid_idx = r.img_out_idx = r.img_in_idx = -1;
         r.dmax_flag = 0;
         if ((rc = step2(ctx, MODE_MODEL, A2, C, F, r, nb, st))) return rc;
         n += 2;
@@ -1267,6 +1294,9 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
   ctx->defaults.tile_z = ((z == 16 && k == 3) || (z == 32 && k == 4)) ? z : 24;
   const char *la = std::getenv("RTM_L2_AHEAD");
   ctx->defaults.l2_ahead = (la && la[0] == '1') ? 1 : 0;
+  // RTM_IMAGE_INPUT=1: backward launches image their input field where they can
+  const char *ii = std::getenv("RTM_IMAGE_INPUT");
+  ctx->defaults.image_input = (ii && ii[0] == '1') ? 1 : 0;
   // RTM_GRAPHS=1 captures each phase of a batch in a CUDA graph by default
   const char *gr = std::getenv("RTM_GRAPHS");
   ctx->defaults.graph = (gr && gr[0] == '1') ? 1 : 0;

@@ -158,7 +158,10 @@ struct Step2RT {
   int img_mid_idx;     // image with the intermediate field (backward); Born:
                        // inject c m S from this snapshot at substep 1
   int img_out_idx;     // image with the output field (backward); Born: at substep 2
-  int dmax_flag;       // 1: reduce max(den) after the mid imaging, 2: after the output
+  int img_in_idx;      // image with the INPUT field v^n (backward; its operands' loads can
+                       // start before the tile copies land)
+  int dmax_flag;       // reduce max(den) after the imaging with 1: the intermediate,
+                       // 2: the output, 3: the input field
   int reverse;         // walk the tile list from its end (snake order over launches)
   int ahead;           // one-tile-per-block kernel: blocks resident at once (each block
                        // prefetches into L2 the tile of the block `ahead` launches later);

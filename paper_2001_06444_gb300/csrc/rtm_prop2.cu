@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(NTH, 3)
   }
   // backward imaging launches: start pulling this thread's num, den and
   // snapshot rows into L2 while the tile loads and the stencil run
-  if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0) && tx < C2X / 4) {
+  if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0 || rt.img_in_idx >= 0) &&
+      tx < C2X / 4) {
     const int j0 = x0 + 4 * tx - g.CP;
     if (j0 >= 0 && j0 < g.SX) {
       const int esz = A.snap_dtype == 0 ? 4 : 2;
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(NTH, 3)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(A.num + po));
           asm volatile("prefetch.global.L2 [%0];" ::"l"(A.den + po));
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int idx = u == 0 ? rt.img_mid_idx : rt.img_out_idx;
+          for (int u = 0; u < 3; ++u) {
+            const int idx = u == 0 ? rt.img_mid_idx : (u == 1 ? rt.img_out_idx : rt.img_in_idx);
             if (idx >= 0) {
               const long long so = ((long long)b * A.nsnap + idx) * g.pplane + (long long)i * g.SX + j0;
               asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char *>(A.snap) +
@@ -263,6 +264,44 @@ __global__ void __launch_bounds__(NTH, 3)
   if (!interior) __syncthreads();  // (block-uniform) the sponge factors are in place
 
   const bool wide = tx < C2X / 4;  // threads that own centre columns
+  float dm = 0.f;                  // running max of den for the max-den reduction
+
+  // imaging with the INPUT field v^n (the centre of the v^n tile)
+  if (MODE == MODE_BWD && rt.img_in_idx >= 0 && wide &&
+      RTM_IN((long long)b * A.nsnap + rt.img_in_idx, A.len.smax, A.err)) {
+    const int j0 = x0 + 4 * tx - g.CP;
+    if (j0 >= 0 && j0 < g.SX) {
+      float sdq, inv;
+      snap_scale(A.snap_dtype, A.smax[(long long)b * A.nsnap + rt.img_in_idx], sdq, inv);
+      const long long sbase = ((long long)b * A.nsnap + rt.img_in_idx) * g.pplane + j0;
+      const long long pbase = (long long)b * g.pplane + j0;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int i = z0 + 3 * ty + r - g.nb;
+        if (i >= 0 && i < g.nz && RTM_IN(sbase + (long long)i * g.SX + 3, A.len.snap, A.err) &&
+            RTM_IN(pbase + (long long)i * g.SX + 3, A.len.items * g.pplane, A.err)) {
+          const float4 w = *reinterpret_cast<const float4 *>(&S.v0[8 + 3 * ty + r][8 + 4 * tx]);
+          const float4 Sv = snap_load4(A.snap, sbase + (long long)i * g.SX, A.snap_dtype, sdq);
+          float4 *pn = reinterpret_cast<float4 *>(A.num + pbase + (long long)i * g.SX);
+          float4 *pd = reinterpret_cast<float4 *>(A.den + pbase + (long long)i * g.SX);
+          float4 nu = *pn, de = *pd;
+          nu.x = fmaf(Sv.x, w.x, nu.x);
+          nu.y = fmaf(Sv.y, w.y, nu.y);
+          nu.z = fmaf(Sv.z, w.z, nu.z);
+          nu.w = fmaf(Sv.w, w.w, nu.w);
+          de.x = fmaf(Sv.x, Sv.x, de.x);
+          de.y = fmaf(Sv.y, Sv.y, de.y);
+          de.z = fmaf(Sv.z, Sv.z, de.z);
+          de.w = fmaf(Sv.w, Sv.w, de.w);
+          *pn = nu;
+          *pd = de;
+          dm = fmaxf(dm, fmaxf(fmaxf(de.x, de.y), fmaxf(de.z, de.w)));
+        }
+      }
+    }
+  }
+  if (MODE == MODE_BWD && rt.dmax_flag == 3)
+    block_max_atomic(dm, &A.dmax[RTM_IN(b, A.len.items, A.err) ? b : 0], S.red);
 
   // deferred half-precision snapshot of the INPUT field v^n (its max was
   // reduced by the launch that produced it)
@@ -361,7 +400,6 @@ __global__ void __launch_bounds__(NTH, 3)
   }
   const int j0 = x0 + 4 * tx - g.CP;  // physical column of this thread's strip
   const bool jok = wide && j0 >= 0 && j0 < g.SX;
-  float dm = 0.f;  // running max of den for the max-den reduction
   if (MODE == MODE_FWD && rt.snap_mid_idx >= 0 && jok) {
     const long long base = ((long long)b * A.nsnap + rt.snap_mid_idx) * g.pplane + j0;
 #pragma unroll

@@ -149,8 +149,8 @@ __device__ __forceinline__ void prefetch_imaging(const Step2Args &A, const Step2
       asm volatile("prefetch.global.L2 [%0];" ::"l"(A.num + po));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(A.den + po));
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int idx = u == 0 ? rt.img_mid_idx : rt.img_out_idx;
+      for (int u = 0; u < 3; ++u) {
+        const int idx = u == 0 ? rt.img_mid_idx : (u == 1 ? rt.img_out_idx : rt.img_in_idx);
         if (idx >= 0) {
           const long long so =
               ((long long)T.b * A.nsnap + idx) * g.pplane + (long long)i * g.SX + j0;
@@ -263,6 +263,62 @@ __device__ __forceinline__ float image4(const Step2Args &A, int b, int idx, int 
   return fmaxf(fmaxf(de.x, de.y), fmaxf(de.z, de.w));
 }
 
+// Imaging with the input field: the snapshot (dequantised), num and den of
+// this thread's centre rows, loaded before the block waits for its tile
+// copies, so their latency overlaps the copies.  ok[r] marks loaded rows.
+template <int R1>
+struct InImg {
+  float4 S[R1 - 1], N[R1 - 1], D[R1 - 1];
+  bool ok[R1 - 1];
+};
+
+template <int R1>
+__device__ __forceinline__ void load_in_imaging(const Step2Args &A, const Step2RT &rt, int t,
+                                                InImg<R1> &p) {
+  constexpr int R2 = R1 - 1;
+  const Geo &g = A.g;
+  const TileRef T = tile_at<R1>(g, t);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j0 = T.x0 + 4 * tx - g.CP;
+  const bool jok = tx < C2X / 4 && j0 >= 0 && j0 < g.SX;
+  const long long ks = (long long)T.b * A.nsnap + rt.img_in_idx;
+  float sdq = 0.f, inv;
+  const bool sok = jok && RTM_IN(ks, A.len.smax, A.err);
+  if (sok) snap_scale(A.snap_dtype, A.smax[ks], sdq, inv);
+#pragma unroll
+  for (int r = 0; r < R2; ++r) {
+    const int i = T.z0 + R2 * ty + r - g.nb;
+    const long long so = ks * g.pplane + (long long)i * g.SX + j0;
+    const long long po = (long long)T.b * g.pplane + (long long)i * g.SX + j0;
+    p.ok[r] = sok && i >= 0 && i < g.nz && RTM_IN(so + 3, A.len.snap, A.err) &&
+              RTM_IN(po + 3, A.len.items * g.pplane, A.err);
+    if (p.ok[r]) {
+      p.S[r] = snap_load4(A.snap, so, A.snap_dtype, sdq);
+      p.N[r] = *reinterpret_cast<const float4 *>(A.num + po);
+      p.D[r] = *reinterpret_cast<const float4 *>(A.den + po);
+    }
+  }
+}
+
+// num += S w, den += S^2 with preloaded operands (the rounding of image4);
+// returns max(den).
+__device__ __forceinline__ float image4_pre(const Step2Args &A, int b, int i, int j0,
+                                            const float4 &w, const float4 &Sv, float4 nu,
+                                            float4 de) {
+  const long long po = (long long)b * A.g.pplane + (long long)i * A.g.SX + j0;
+  nu.x = fmaf(Sv.x, w.x, nu.x);
+  nu.y = fmaf(Sv.y, w.y, nu.y);
+  nu.z = fmaf(Sv.z, w.z, nu.z);
+  nu.w = fmaf(Sv.w, w.w, nu.w);
+  de.x = fmaf(Sv.x, Sv.x, de.x);
+  de.y = fmaf(Sv.y, Sv.y, de.y);
+  de.z = fmaf(Sv.z, Sv.z, de.z);
+  de.w = fmaf(Sv.w, Sv.w, de.w);
+  *reinterpret_cast<float4 *>(A.num + po) = nu;
+  *reinterpret_cast<float4 *>(A.den + po) = de;
+  return fmaxf(fmaxf(de.x, de.y), fmaxf(de.z, de.w));
+}
+
 // FP32 snapshot of 4 physical columns (columns past nx stored as zero).
 __device__ __forceinline__ void snap_f32(const Step2Args &A, int b, int idx, int i, int j0,
                                          float4 v) {
@@ -277,7 +333,7 @@ __device__ __forceinline__ void snap_f32(const Step2Args &A, int b, int idx, int
 // One tile: both substeps, the fused work of steps n+1 and n+2, the stores.
 template <int MODE, int R1>
 __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2Args &A,
-                                          const Step2RT &rt, int t) {
+                                          const Step2RT &rt, int t, const InImg<R1> *pre) {
   constexpr int EZ = Shape<R1>::EZ, C2Z = Shape<R1>::C2Z, R2 = Shape<R1>::R2;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const Geo &g = A.g;
@@ -313,6 +369,24 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
       }
     }
   }
+
+  // imaging with the INPUT field v^n (the centre of the v^n tile), before
+  // substep 1 overwrites it; operands preloaded by the caller when it can
+  float dm = 0.f;  // running max of den for the max-den reduction
+  if (MODE == MODE_BWD && rt.img_in_idx >= 0 && jok) {
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+      const int i = z0 + R2 * ty + r - g.nb;
+      const float4 w = *reinterpret_cast<const float4 *>(&S.v0[8 + R2 * ty + r][8 + 4 * tx]);
+      if (pre) {
+        if (pre->ok[r]) dm = fmaxf(dm, image4_pre(A, b, i, j0, w, pre->S[r], pre->N[r], pre->D[r]));
+      } else if (i >= 0 && i < g.nz) {
+        dm = fmaxf(dm, image4(A, b, rt.img_in_idx, i, j0, w));
+      }
+    }
+  }
+  if (MODE == MODE_BWD && rt.dmax_flag == 3)
+    block_max_atomic(dm, &A.dmax[RTM_IN(b, A.len.items, A.err) ? b : 0], red);
 
   // ---- substep 1 (a warp whose rows lie 4 or more past the grid skips:
   // substep 2 reads rows up to 4 past its own, and computes none below the
@@ -386,7 +460,6 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
         ro[en.y] = v1_at<R1>(S, en.x);
     }
   }
-  float dm = 0.f;  // running max of den for the max-den reduction
   if (MODE == MODE_FWD && rt.snap_mid_idx >= 0 && jok) {
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
@@ -552,7 +625,8 @@ __global__ void __launch_bounds__(NTH, 2)
   }
   __syncthreads();
   issue_tile<R1>(S.st[0], &S.bar[0], &map_v, &map_d, &map_c, A, tile_index(0));
-  const bool imaging = MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0);
+  const bool imaging =
+      MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0 || rt.img_in_idx >= 0);
   if (imaging) prefetch_imaging<R1>(A, rt, tile_index(0));
   for (int k = 0; (int)blockIdx.x + k * G < ntiles; ++k) {
     const int s = k & 1;
@@ -572,7 +646,7 @@ __global__ void __launch_bounds__(NTH, 2)
       if (has_next) mbar_wait_bounded(&S.bar[s ^ 1], (unsigned)((k + 1) >> 1) & 1u, kWaitNs);
       return;
     }
-    tile_body<MODE, R1>(S.st[s], S.red, A, rt, tile_index(k));
+    tile_body<MODE, R1>(S.st[s], S.red, A, rt, tile_index(k), nullptr);
     // generic-proxy writes of this stage (d in place, v^{n+1}) are ordered
     // before the copy engine's next writes into it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -611,13 +685,16 @@ __global__ void __launch_bounds__(NTH, 3)
   issue_tile<R1>(S.st, &S.bar, &map_v, &map_d, &map_c, A, t);
   if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0))
     prefetch_imaging<R1>(A, rt, t);
+  // imaging with the input field: its operands load while the tile copies land
+  InImg<R1> pre;
+  if (MODE == MODE_BWD && rt.img_in_idx >= 0) load_in_imaging<R1>(A, rt, t, pre);
   const bool ok = mbar_wait_bounded(&S.bar, 0, kWaitNs);
   if (__syncthreads_or(!ok)) {  // (block-wide; also orders the staged sponge factors)
     if (tid == 0) atomicExch(A.err, 1);
     mbar_wait_bounded(&S.bar, 0, kWaitNs);  // let the copies in flight land (bounded)
     return;
   }
-  tile_body<MODE, R1>(S.st, S.red, A, rt, t);
+  tile_body<MODE, R1>(S.st, S.red, A, rt, t, MODE == MODE_BWD && rt.img_in_idx >= 0 ? &pre : nullptr);
 }
 
 size_t step2p_smem_bytes(int tile_z) {
