@@ -58,6 +58,8 @@ def parse():
                    help="with --kernel 3 (16, 24) or 4 (24, 32): centre rows of a tile")
     p.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                    help="with --kernel 1-3: capture each phase in a CUDA graph")
+    p.add_argument("--pdl", type=int, default=0, choices=[0, 1],
+                   help="with --kernel 4: programmatic dependent launches")
     p.add_argument("--image-input", type=int, default=0, choices=[0, 1],
                    help="with --kernel 2-4: backward launches image their input field")
     p.add_argument("--l2-ahead", type=int, default=0, choices=[0, 1],
@@ -256,6 +258,7 @@ def run_native(args, world, rank, local):
         os.environ["RTM_GRAPHS"] = str(args.graphs)
         os.environ["RTM_L2_AHEAD"] = str(args.l2_ahead)
         os.environ["RTM_IMAGE_INPUT"] = str(args.image_input)
+        os.environ["RTM_PDL"] = str(args.pdl)
     ctx = rtm.Context(local)
     ctx.model(grid, vel_true, acq, -1, seis)  # observed data, untimed
     torch.cuda.synchronize()
@@ -265,7 +268,7 @@ def run_native(args, world, rank, local):
         tuned = {"step_kernel": args.kernel, "max_items": args.batch, "graph": args.graphs,
                  "tile_z": args.tile_z if args.kernel in (3, 4) else 24,
                  "l2_ahead": args.l2_ahead if args.kernel == 2 else 0,
-                 "image_input": args.image_input, "fixed": True}
+                 "image_input": args.image_input, "pdl": args.pdl, "fixed": True}
     else:
         tuned = ctx.autotune(grid, acq, opts, trial_steps=64)  # untimed: picks the launch config
     for _ in range(args.warmup):

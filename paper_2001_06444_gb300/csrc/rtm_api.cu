@@ -446,6 +446,7 @@ struct Common {
   int nsample = 1;
   int kernel = 2;  // RunConfig::step_kernel of the call
   int l2_ahead = 0;  // RunConfig::l2_ahead of the call
+  int pdl = 0;       // RunConfig::pdl of the call
   long long n_rent = 0, n_rext = 0, n_rcen = 0;  // receiver-table entries (debug index checks)
   DevBuf c_all, gx, gz, src_rc, rptr, rent, rext_ptr, rext_ent, rcen_ptr, rcen_ent, wav, items, err;
   CUtensorMap mc;
@@ -489,10 +490,11 @@ static void step2_receiver_lists(const Geo &g, const rtm_acq &acq, std::vector<i
 // Upload the per-call tables shared by all items.
 static int setup_common(rtm_ctx *ctx, Common &C, const rtm_grid &gr, const rtm_acq &acq,
                         int nsample, const float *vel_d, cudaStream_t st, int step_kernel,
-                        int tile_z, int l2_ahead) {
+                        int tile_z, int l2_ahead, int pdl) {
   C.g = make_geo(gr, step_kernel >= 3 ? tile_z : 24);
   C.kernel = step_kernel;
   C.l2_ahead = l2_ahead;
+  C.pdl = pdl;
   C.k = make_coef(gr);
   C.nsample = nsample;
   const Geo &g = C.g;
@@ -678,6 +680,7 @@ static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields 
   Step2RT r = rt;
   r.reverse = F.n2 & 1;
   r.ahead = C.l2_ahead;
+  r.pdl = C.kernel == 4 && C.pdl;
   if (C.kernel == 3)
     CU(launch_step2p(mode, C.g.tz2, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
   else if (C.kernel == 4)
@@ -738,7 +741,7 @@ int migrate_device(rtm_ctx *ctx, const rtm_grid &gr, int nsample, const float *v
   {
     PhaseRange ph("setup");
     rc = setup_common(ctx, C, gr, acq, nsample, vel_d, st, cfg.step_kernel, cfg.tile_z,
-                      cfg.l2_ahead);
+                      cfg.l2_ahead, cfg.pdl);
   }
   if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
@@ -1102,7 +1105,7 @@ static int model_device(rtm_ctx *ctx, const rtm_grid &gr, const float *vel_d,
   const int sk = ctx->defaults.step_kernel;
   Common C;
   int rc = setup_common(ctx, C, gr, acq, 1, vel_d, st, sk, ctx->defaults.tile_z,
-                        ctx->defaults.l2_ahead);
+                        ctx->defaults.l2_ahead, ctx->defaults.pdl);
   if (!rc) rc = maybe_inject_timeout(ctx, C, st);
   if (rc) return rc;
   const Geo &g = C.g;
@@ -1297,6 +1300,9 @@ int rtm_ctx_create(rtm_ctx **out, int device, size_t hbm_budget_bytes) {
   // RTM_IMAGE_INPUT=1: backward launches image their input field where they can
   const char *ii = std::getenv("RTM_IMAGE_INPUT");
   ctx->defaults.image_input = (ii && ii[0] == '1') ? 1 : 0;
+  // RTM_PDL=1: the kernel-4 launches are programmatic dependents of the previous one
+  const char *pd = std::getenv("RTM_PDL");
+  ctx->defaults.pdl = (pd && pd[0] == '1') ? 1 : 0;
   // RTM_GRAPHS=1 captures each phase of a batch in a CUDA graph by default
   const char *gr = std::getenv("RTM_GRAPHS");
   ctx->defaults.graph = (gr && gr[0] == '1') ? 1 : 0;

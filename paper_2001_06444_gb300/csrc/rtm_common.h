@@ -163,6 +163,8 @@ struct Step2RT {
   int dmax_flag;       // reduce max(den) after the imaging with 1: the intermediate,
                        // 2: the output, 3: the input field
   int reverse;         // walk the tile list from its end (snake order over launches)
+  int pdl;             // launched as a programmatic dependent of the previous launch: read
+                       // its outputs only after griddepcontrol.wait
   int ahead;           // one-tile-per-block kernel: blocks resident at once (each block
                        // prefetches into L2 the tile of the block `ahead` launches later);
                        // 0 = no prefetch

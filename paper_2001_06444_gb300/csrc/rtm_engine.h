@@ -30,6 +30,7 @@ struct RunConfig {
   int tile_z = 24;      // centre rows of a two-step tile (16 with kernel 3, 32 with kernel 4)
   int l2_ahead = 0;     // step_kernel 2: each block prefetches a later block's tile into L2
   int image_input = 0;  // two-step backward launches image their input field where they can
+  int pdl = 0;          // step_kernel 4: programmatic dependent launches (griddepcontrol)
 };
 // Shape key of the autotuner cache.
 struct TuneKey {

@@ -682,7 +682,34 @@ __global__ void __launch_bounds__(NTH, 3)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  issue_tile<R1>(S.st, &S.bar, &map_v, &map_d, &map_c, A, t);
+  if (rt.pdl) {
+    // launched as a programmatic dependent: copy what the previous launch does
+    // not write (c, the sponge factors) while it finishes, then wait for it
+    // before the copies of its output fields v^n, d^n
+    const TileRef T = tile_at<R1>(A.g, t);
+    if (tid == 0) {
+      const int smp = A.one_sample ? 0 : A.item_sample[T.b];
+      (void)RTM_IN(smp, A.len.nsample, A.err);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar)),
+                   "r"(Shape<R1>::kTx)
+                   : "memory");
+      tma_load_3d(&S.st.c[0][0], &map_c, T.x0 - 4, T.z0 - 4, smp, &S.bar);
+    }
+    if (!tile_interior<R1>(A.g, T.x0, T.z0)) {
+      if (tid < EX) S.st.gxs[tid] = A.gx[min(max(T.x0 - 4 + tid, 0), A.g.P - 1)];
+      if (tid < Shape<R1>::EZ) S.st.gzs[tid] = A.gz[min(max(T.z0 - 4 + tid, 0), A.g.NZ - 1)];
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // every block of this launch has started: the next launch may begin its own
+    // preamble on the SMs this launch frees
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (tid == 0) {
+      tma_load_3d(&S.st.v0[0][0], &map_v, T.x0 - 8, T.z0 - 8, T.b, &S.bar);
+      tma_load_3d(&S.st.d[0][0], &map_d, T.x0 - 4, T.z0 - 4, T.b, &S.bar);
+    }
+  } else {
+    issue_tile<R1>(S.st, &S.bar, &map_v, &map_d, &map_c, A, t);
+  }
   if (MODE == MODE_BWD && (rt.img_mid_idx >= 0 || rt.img_out_idx >= 0))
     prefetch_imaging<R1>(A, rt, t);
   // imaging with the input field: its operands load while the tile copies land
@@ -721,8 +748,23 @@ cudaError_t launch_step2a(int mode, int tile_z, const CUtensorMap &mv, const CUt
       if (e != cudaSuccess) return e;
       attr_set[slot].store(true, std::memory_order_release);
     }
-    kernel<<<(unsigned)ntl, block, smem, st>>>(mv, md, mc, A, rt, (int)ntl);
-    return cudaGetLastError();
+    if (!rt.pdl) {
+      kernel<<<(unsigned)ntl, block, smem, st>>>(mv, md, mc, A, rt, (int)ntl);
+      return cudaGetLastError();
+    }
+    // programmatic dependent launch: blocks may start while the previous
+    // kernel on the stream finishes (the kernel waits before reading its outputs)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ntl);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, mv, md, mc, A, rt, (int)ntl);
   };
   const int h = tile_z == 32 ? 4 : 0;
   switch (mode) {

@@ -359,14 +359,16 @@ def _env_context(**env):
 
 # the two-step kernels: one tile per block (with and without its L2 prefetch
 # of later tiles); persistent with 24- and 16-row tiles; one tile per block
-# with v^{n+1} over v^n, 24- and 32-row tiles; and backward launches that
-# image their input field (RTM_IMAGE_INPUT=1) with each kernel
+# with v^{n+1} over v^n, 24- and 32-row tiles; backward launches that image
+# their input field (RTM_IMAGE_INPUT=1) with each kernel; and programmatic
+# dependent launches (RTM_PDL=1)
 TWO_STEP_KERNELS = [dict(RTM_STEP_KERNEL=2), dict(RTM_STEP_KERNEL=2, RTM_L2_AHEAD=1),
                     dict(RTM_STEP_KERNEL=3), dict(RTM_STEP_KERNEL=3, RTM_TILE_Z=16),
                     dict(RTM_STEP_KERNEL=4), dict(RTM_STEP_KERNEL=4, RTM_TILE_Z=32),
                     dict(RTM_STEP_KERNEL=2, RTM_IMAGE_INPUT=1),
                     dict(RTM_STEP_KERNEL=3, RTM_IMAGE_INPUT=1),
-                    dict(RTM_STEP_KERNEL=4, RTM_TILE_Z=32, RTM_IMAGE_INPUT=1)]
+                    dict(RTM_STEP_KERNEL=4, RTM_TILE_Z=32, RTM_IMAGE_INPUT=1),
+                    dict(RTM_STEP_KERNEL=4, RTM_TILE_Z=32, RTM_PDL=1)]
 
 
 @pytest.mark.parametrize("nz", [90, 47])
