@@ -680,7 +680,8 @@ static int step2(rtm_ctx *ctx, int mode, Step2Args &A2, const Common &C, Fields 
   Step2RT r = rt;
   r.reverse = F.n2 & 1;
   r.ahead = C.l2_ahead;
-  r.pdl = C.kernel == 4 && C.pdl;
+  // (programmatic dependent launches are built for the migration's phases)
+  r.pdl = C.kernel == 4 && C.pdl && (mode == MODE_FWD || mode == MODE_BWD);
   if (C.kernel == 3)
     CU(launch_step2p(mode, C.g.tz2, F.mv[F.cv], F.md[F.cd], C.mc, A2, r, nb, st));
   else if (C.kernel == 4)

@@ -331,7 +331,9 @@ __device__ __forceinline__ void snap_f32(const Step2Args &A, int b, int idx, int
 }
 
 // One tile: both substeps, the fused work of steps n+1 and n+2, the stores.
-template <int MODE, int R1>
+// IN_IMG compiles in the imaging with the input field (rt.img_in_idx, dmax
+// flag 3); instances without it must not be launched with either set.
+template <int MODE, int R1, bool IN_IMG>
 __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2Args &A,
                                           const Step2RT &rt, int t, const InImg<R1> *pre) {
   constexpr int EZ = Shape<R1>::EZ, C2Z = Shape<R1>::C2Z, R2 = Shape<R1>::R2;
@@ -373,7 +375,7 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
   // imaging with the INPUT field v^n (the centre of the v^n tile), before
   // substep 1 overwrites it; operands preloaded by the caller when it can
   float dm = 0.f;  // running max of den for the max-den reduction
-  if (MODE == MODE_BWD && rt.img_in_idx >= 0 && jok) {
+  if (IN_IMG && MODE == MODE_BWD && rt.img_in_idx >= 0 && jok) {
 #pragma unroll
     for (int r = 0; r < R2; ++r) {
       const int i = z0 + R2 * ty + r - g.nb;
@@ -385,7 +387,7 @@ __device__ __forceinline__ void tile_body(Stage<R1> &S, float *red, const Step2A
       }
     }
   }
-  if (MODE == MODE_BWD && rt.dmax_flag == 3)
+  if (IN_IMG && MODE == MODE_BWD && rt.dmax_flag == 3)
     block_max_atomic(dm, &A.dmax[RTM_IN(b, A.len.items, A.err) ? b : 0], red);
 
   // ---- substep 1 (a warp whose rows lie 4 or more past the grid skips:
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(NTH, 2)
       if (has_next) mbar_wait_bounded(&S.bar[s ^ 1], (unsigned)((k + 1) >> 1) & 1u, kWaitNs);
       return;
     }
-    tile_body<MODE, R1>(S.st[s], S.red, A, rt, tile_index(k), nullptr);
+    tile_body<MODE, R1, true>(S.st[s], S.red, A, rt, tile_index(k), nullptr);
     // generic-proxy writes of this stage (d in place, v^{n+1}) are ordered
     // before the copy engine's next writes into it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -665,7 +667,10 @@ struct Smem1 {
   float red[NTH / 32];
 };
 
-template <int MODE, int R1>
+// VAR bit 0: imaging with the input field, its operands loaded before the
+// tile wait (backward); bit 1: launched as a programmatic dependent.  The
+// default launch (VAR 0) carries neither path's code.
+template <int MODE, int R1, int VAR>
 __global__ void __launch_bounds__(NTH, 3)
     k_step2a(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_d,
              const __grid_constant__ CUtensorMap map_c, const Step2Args A, const Step2RT rt,
@@ -681,8 +686,9 @@ __global__ void __launch_bounds__(NTH, 3)
                  : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  constexpr bool IN_IMG = (VAR & 1) != 0, PDL = (VAR & 2) != 0;
   __syncthreads();
-  if (rt.pdl) {
+  if constexpr (PDL) {
     // launched as a programmatic dependent: copy what the previous launch does
     // not write (c, the sponge factors) while it finishes, then wait for it
     // before the copies of its output fields v^n, d^n
@@ -714,14 +720,15 @@ __global__ void __launch_bounds__(NTH, 3)
     prefetch_imaging<R1>(A, rt, t);
   // imaging with the input field: its operands load while the tile copies land
   InImg<R1> pre;
-  if (MODE == MODE_BWD && rt.img_in_idx >= 0) load_in_imaging<R1>(A, rt, t, pre);
+  if (IN_IMG && MODE == MODE_BWD && rt.img_in_idx >= 0) load_in_imaging<R1>(A, rt, t, pre);
   const bool ok = mbar_wait_bounded(&S.bar, 0, kWaitNs);
   if (__syncthreads_or(!ok)) {  // (block-wide; also orders the staged sponge factors)
     if (tid == 0) atomicExch(A.err, 1);
     mbar_wait_bounded(&S.bar, 0, kWaitNs);  // let the copies in flight land (bounded)
     return;
   }
-  tile_body<MODE, R1>(S.st, S.red, A, rt, t, MODE == MODE_BWD && rt.img_in_idx >= 0 ? &pre : nullptr);
+  tile_body<MODE, R1, IN_IMG>(S.st, S.red, A, rt, t,
+                              IN_IMG && MODE == MODE_BWD && rt.img_in_idx >= 0 ? &pre : nullptr);
 }
 
 size_t step2p_smem_bytes(int tile_z) {
@@ -738,7 +745,12 @@ cudaError_t launch_step2a(int mode, int tile_z, const CUtensorMap &mv, const CUt
   if (tile_z != 24 && tile_z != 32) return cudaErrorInvalidValue;
   const long long ntl = (long long)B * A.g.ntx2 * A.g.ntz2;
   if (ntl < 1 || ntl > 0x7fffffffLL) return cudaErrorInvalidValue;
-  static std::atomic<bool> attr_set[8];
+  // the input-field imaging and programmatic-dependent instances exist for the
+  // backward and forward migration phases only
+  const bool in_img = rt.img_in_idx >= 0 || rt.dmax_flag == 3;
+  if (in_img && mode != MODE_BWD) return cudaErrorInvalidValue;
+  if (rt.pdl && mode != MODE_BWD && mode != MODE_FWD) return cudaErrorInvalidValue;
+  static std::atomic<bool> attr_set[32];
   const size_t smem = step2a_smem_bytes(tile_z);
   dim3 block(32, NTH / 32);
   auto launch = [&](auto kernel, int slot) -> cudaError_t {
@@ -766,13 +778,29 @@ cudaError_t launch_step2a(int mode, int tile_z, const CUtensorMap &mv, const CUt
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, mv, md, mc, A, rt, (int)ntl);
   };
-  const int h = tile_z == 32 ? 4 : 0;
-  switch (mode) {
-    case MODE_FWD: return h ? launch(k_step2a<MODE_FWD, 5>, 4) : launch(k_step2a<MODE_FWD, 4>, 0);
-    case MODE_MODEL: return h ? launch(k_step2a<MODE_MODEL, 5>, 5) : launch(k_step2a<MODE_MODEL, 4>, 1);
-    case MODE_BWD: return h ? launch(k_step2a<MODE_BWD, 5>, 6) : launch(k_step2a<MODE_BWD, 4>, 2);
-    case MODE_BORN: return h ? launch(k_step2a<MODE_BORN, 5>, 7) : launch(k_step2a<MODE_BORN, 4>, 3);
+  // slot = 16 * (tile_z == 32) + 4 * mode + VAR
+  const int var = (in_img ? 1 : 0) | (rt.pdl ? 2 : 0);
+  const int slot = (tile_z == 32 ? 16 : 0) + 4 * mode + var;
+#define RTM_S2A(M, R, V) launch(k_step2a<M, R, V>, (R == 5 ? 16 : 0) + 4 * M + V)
+  switch (slot) {
+    case 0: return RTM_S2A(MODE_FWD, 4, 0);
+    case 2: return RTM_S2A(MODE_FWD, 4, 2);
+    case 4: return RTM_S2A(MODE_MODEL, 4, 0);
+    case 8: return RTM_S2A(MODE_BWD, 4, 0);
+    case 9: return RTM_S2A(MODE_BWD, 4, 1);
+    case 10: return RTM_S2A(MODE_BWD, 4, 2);
+    case 11: return RTM_S2A(MODE_BWD, 4, 3);
+    case 12: return RTM_S2A(MODE_BORN, 4, 0);
+    case 16: return RTM_S2A(MODE_FWD, 5, 0);
+    case 18: return RTM_S2A(MODE_FWD, 5, 2);
+    case 20: return RTM_S2A(MODE_MODEL, 5, 0);
+    case 24: return RTM_S2A(MODE_BWD, 5, 0);
+    case 25: return RTM_S2A(MODE_BWD, 5, 1);
+    case 26: return RTM_S2A(MODE_BWD, 5, 2);
+    case 27: return RTM_S2A(MODE_BWD, 5, 3);
+    case 28: return RTM_S2A(MODE_BORN, 5, 0);
   }
+#undef RTM_S2A
   return cudaErrorInvalidValue;
 }
 
