@@ -22,8 +22,11 @@
  *      any coefficient outside the significant prefix has its bit set, and
  *      a scan then moves the prefix up to that coefficient;
  *   5. the bits of each significant coefficient below the plane at which it
- *      entered the prefix, lowest plane first, then its sign (when its kept
- *      magnitude is not zero), after the significance section of the block;
+ *      entered the prefix, lowest plane first, then a sign bit (1 for a
+ *      negative coefficient whose kept magnitude is not zero, else 0), after
+ *      the significance section of the block: every member carries a sign
+ *      bit, so the significance section alone fixes the length of the
+ *      refinement section;
  *   6. kmin, the lowest plane kept: the largest k >= 1 with
  *      16 2^k + 21.5 <= tol 2^(28 - e), else 0 (all planes); lossless 0.
  * Fixed accuracy decodes every element within max(tol, 2^(e - 23)) of its
@@ -33,7 +36,7 @@
  * 2^(e - 24).  Lossless decoding returns the input bits exactly.
  *
  * Stream of one array (little endian): 64-byte header {u32 magic "RTMZ",
- * u32 version 2, u32 mode (0 fixed accuracy, 1 lossless), u32 blocks per
+ * u32 version 3, u32 mode (0 fixed accuracy, 1 lossless), u32 blocks per
  * chunk (32), i64 n0, i64 n1, f64 tol, u64 words of the bit section, u64
  * chunks, u64 0}; the u32 word offset of every chunk of 32 blocks, padded
  * with zeros to a multiple of four entries; the bit section as u32 words,
@@ -179,7 +182,7 @@ static void encode_planes(const uint64_t *m, const int *neg, int top, int kmin, 
   }
   for (int i = 0; i < n; ++i) {
     for (int k = kmin; k < entry[i]; ++k) put(bw, (int)((m[i] >> k) & 1u));
-    if (m[i] >> kmin) put(bw, neg[i]);
+    put(bw, (m[i] >> kmin) ? neg[i] : 0);
   }
 }
 
@@ -204,7 +207,8 @@ static int decode_planes(bitr *br, uint64_t *m, int *neg, int top, int kmin) {
   for (int i = 0; i < n; ++i) {
     for (int k = kmin; k < entry[i]; ++k)
       if (get(br)) m[i] |= (uint64_t)1 << k;
-    if (m[i] >> kmin) neg[i] = get(br);
+    const int sg = get(br);
+    if (m[i] >> kmin) neg[i] = sg;
   }
   return br->bad ? -1 : 0;
 }
@@ -326,7 +330,7 @@ uint64_t oracle_codec_compress(const float *data, int64_t n0, int64_t n1, double
     encode_block(x, tol, &bw);
   }
   const uint64_t nwords = (bw.pos + 31) / 32;
-  const uint32_t head[4] = {0x5A4D5452u, 2u, tol > 0 ? 0u : 1u, CZ_CHUNK};
+  const uint32_t head[4] = {0x5A4D5452u, 3u, tol > 0 ? 0u : 1u, CZ_CHUNK};
   const uint64_t tail[3] = {nwords, (uint64_t)nc, 0};
   memcpy(out + 0, head, 16);
   memcpy(out + 16, &n0, 8);
@@ -351,7 +355,7 @@ int oracle_codec_decompress(const unsigned char *in, uint64_t nbytes, float *dat
   memcpy(&tol, in + 32, 8);
   memcpy(tail, in + 40, 16);
   const int64_t nb1 = (n1 + 3) / 4, nb = ((n0 + 3) / 4) * nb1, nc = nchunks(n0, n1);
-  if (head[0] != 0x5A4D5452u || head[1] != 2u || head[3] != CZ_CHUNK || m0 != n0 || m1 != n1 ||
+  if (head[0] != 0x5A4D5452u || head[1] != 3u || head[3] != CZ_CHUNK || m0 != n0 || m1 != n1 ||
       tail[1] != (uint64_t)nc || (head[2] == 0) != (tol > 0) || head[2] > 1)
     return -2;
   const uint64_t start = CZ_HEADER + 16 * ((uint64_t)(nc + 3) / 4);

@@ -3,7 +3,7 @@
 // used in fixed-accuracy and lossless modes between the workflow's stages).
 //
 // Stream of one array (little endian): a 64-byte header {u32 magic "RTMZ",
-// u32 version 2, u32 mode (0 fixed accuracy, 1 lossless), u32 blocks per
+// u32 version 3, u32 mode (0 fixed accuracy, 1 lossless), u32 blocks per
 // chunk (32), i64 n0, i64 n1, f64 tol, u64 words of the bit section, u64
 // chunks, u64 0}; the u32 word offset of every chunk of 32 blocks (zero
 // padded to a multiple of four entries); the bit section, u32 words, bits
@@ -17,7 +17,9 @@
 // order, magnitudes coded from plane 30 (lossless 32) down to kmin with
 // prefix significance (a group test per plane, a scan to the next
 // significant coefficient), then, per significant coefficient, its bits
-// below the plane where it entered the prefix (lowest first) and its sign.
+// below the plane where it entered the prefix (lowest first) and a sign bit
+// (0 when its kept magnitude is zero): the significance section alone fixes
+// the length of the refinement section.
 // kmin is the largest k >= 1 with 16 2^k + 21.5 <= tol 2^(28-e), else 0.
 //
 // Encoding, in three passes with no device-side waiting:
@@ -31,10 +33,14 @@
 //      the stream's byte count;
 //   3. one CTA per tile copies its words to their offset and writes the
 //      offsets of its chunks.
-// Decoding: a warp owns 32 chunks; each lane first walks one chunk to find
-// the bit offset of each of its blocks, then the warp decodes the chunks one
-// at a time, one block per lane, from the chunk's words staged in shared
-// memory, with coalesced stores.
+// Decoding, per group of arrays, in two passes with no device-side waiting:
+//   1. the walk: one thread per chunk (a CTA's chunks ordered by size first)
+//      finds the bit offset and the cost class (events, members) of every
+//      block; the CTA lists its blocks that are not all zero in class order
+//      (a segment of the decode's list) and writes its all-zero blocks to
+//      the output, row by row;
+//   2. the decode: a CTA per segment, one block per thread in list order,
+//      so that the lanes of a warp run the same loops for as many trips.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,9 +64,17 @@ constexpr int kTile = kChunk * kWarps;   // blocks per encoder tile (one CTA)
 constexpr int kBlockWords = 20;          // 640 bits bound one coded block
 constexpr int kChunkWords = kChunk * kBlockWords;
 constexpr int kTileWords = kTile * kBlockWords;
-constexpr int kDecWarps = 4;             // decoder: warps per CTA, 32 chunks per warp
+constexpr int kWalk = 256;               // decoder's walk: chunks per CTA, one per thread
+constexpr int kWalkKeys = 64;            // size classes the walk orders chunks by
+constexpr int kSeg = kWalk * kChunk;     // blocks of a walk CTA: a segment of the decode's list
+constexpr int kClasses = 256;            // decode cost classes (0: all-zero blocks)
+constexpr int kDec = 256;                // decoder: threads per CTA, one block per thread
+constexpr u64 kGroupBlocks = 1ull << 24; // list entries per group of arrays
+static_assert(kClasses == kWalk, "one class count per walk thread");
+static_assert(kSeg <= (1 << 13), "a segment's block index takes 13 bits of a list entry");
 constexpr int kHeader = 64;
 constexpr u32 kMagic = 0x5A4D5452u;
+constexpr u32 kVersion = 3;
 constexpr int kTab = 288;                // kmin by e + 150, e in [-150, 137]
 
 __host__ __device__ constexpr int perm(int i) {
@@ -102,6 +116,12 @@ struct DecArgs {
   u64 stride, index_bytes;
   const unsigned char *kmin;  // [count][kTab]
   int *err;  // [0] malformed flag, [1] first malformed array
+  u32 arr0;       // first array of this group (error reports)
+  u32 count;      // arrays in this group
+  u32 nseg;       // segments (kWalk chunks, kSeg blocks) per array
+  u32 *list;      // [count][nseg][kSeg] per segment: its blocks not all zero, in class
+                  // order: index in the segment << 15 | bit offset in the chunk
+  u32 *segcount;  // [count][nseg] entries of each segment's list
 };
 
 // kmin for every block exponent of a tolerance: the largest k in [1, 30]
@@ -283,7 +303,7 @@ struct Block {
       refine += mem ? s[i] - kmin : 0;
       plast = mem ? s[i] : plast;
     }
-    refine += __popc(nz);
+    refine += cur;  // a sign bit per member
     const int nev = __popc(ev);
     const int sig = cur == 0 ? Ktop - kmin + 1
                              : nev + cur + (Ktop - plast) + (cur < 16 ? plast - kmin + 1 : 0);
@@ -320,13 +340,12 @@ struct Block {
         const u64 t = (u64)(m[i] >> kmin);
         const u64 field = t & ((1ull << w) - 1ull);
         const u64 sg = (neg >> i) & 1u;
+        const u64 sgk = sg & (nz >> i);  // the sign of a zero kept magnitude is 0
         if (LL) {
           bw.put(field, w);
-          if ((nz >> i) & 1u) bw.put(sg, 1);
-        } else if ((nz >> i) & 1u) {
-          bw.put(field | (sg << w), w + 1);
+          bw.put(sgk, 1);
         } else {
-          bw.put(0, w);
+          bw.put(field | (sgk << w), w + 1);
         }
       }
     }
@@ -359,10 +378,7 @@ struct Block {
       const int w = ss[i * stride] - kmin;  // <= 30
       const u32 t = ms[i * stride] >> kmin;
       const u32 field = t & ((1u << w) - 1u);
-      if ((nz >> i) & 1u)
-        bw.put(field | (((neg >> i) & 1u) << w), w + 1);
-      else
-        bw.put(0, w);
+      bw.put(field | (((neg & nz) >> i & 1u) << w), w + 1);
     }
     bw.flush();
   }
@@ -487,7 +503,7 @@ __global__ void __launch_bounds__(1024) k_cz_scan(const __grid_constant__ EncArg
     for (u32 i = a.nchunk; i < (u32)(a.index_bytes / 4); ++i) index[i] = 0;
     u32 *h = reinterpret_cast<u32 *>(slot);
     h[0] = bad ? 0u : kMagic;
-    h[1] = 2u;
+    h[1] = kVersion;
     h[2] = LL ? 1u : 0u;
     h[3] = kChunk;
     long long *hl = reinterpret_cast<long long *>(slot + 16);
@@ -527,27 +543,42 @@ __global__ void __launch_bounds__(kTile) k_cz_place(const __grid_constant__ EncA
 
 // ---------------------------------------------------------------- decode --
 
-// Sequential reader over global words [.., end) of one chunk (phase 1).
+// Sequential reader over the words of one chunk in global memory (the walk);
+// positions count bits from the chunk's first bit, reads past its end see
+// zeros.  At least 32 bits are buffered after every call, and the word after
+// the buffered ones is already loading.
 struct GReader {
   const u32 *w;
-  u64 nw, widx, pos, end;
-  u64 buf;
+  u32 nw, widx, pos;
   int avail;
-  __device__ void init(const u32 *words, u64 nwords, u64 start) {
+  u64 buf;
+  u32 nxt;  // word widx - 1
+  __device__ __forceinline__ void init(const u32 *words, u32 nwords) {
     w = words;
     nw = nwords;
-    widx = start;
-    pos = start * 32;
-    end = nwords * 32;
-    buf = 0;
-    avail = 0;
-    refill();
+    buf = nw > 0 ? __ldg(w) : 0u;
+    nxt = nw > 1 ? __ldg(w + 1) : 0u;
+    avail = 32;
+    widx = 2;
+    pos = 0;
+  }
+  // start at bit `bit` of the chunk (the decode)
+  __device__ __forceinline__ void init_at(const u32 *words, u32 nwords, u32 bit) {
+    w = words;
+    nw = nwords;
+    const u32 wi = bit >> 5;
+    const u32 a0 = wi < nw ? __ldg(w + wi) : 0u, a1 = wi + 1 < nw ? __ldg(w + wi + 1) : 0u;
+    buf = (((u64)a1 << 32) | a0) >> (bit & 31);
+    avail = 64 - (int)(bit & 31);
+    nxt = wi + 2 < nw ? __ldg(w + wi + 2) : 0u;
+    widx = wi + 3;
+    pos = bit;
   }
   __device__ __forceinline__ void refill() {
     if (avail <= 32) {
-      const u32 v = widx < nw ? __ldg(w + widx) : 0u;
-      buf |= (u64)v << avail;
+      buf |= (u64)nxt << avail;
       avail += 32;
+      nxt = widx < nw ? __ldg(w + widx) : 0u;
       widx++;
     }
   }
@@ -555,23 +586,16 @@ struct GReader {
   __device__ __forceinline__ void skip(int n) {  // n <= 32
     buf >>= n;
     avail -= n;
-    pos += n;
+    pos += (u32)n;
     refill();
   }
-  __device__ bool overrun() const { return pos > end; }
-};
-
-// Random-access reader over a chunk's words staged in shared memory (phase 2);
-// w[nw] and w[nw + 1] are zero, so reads past the end see zeros.
-struct SReader {
-  const u32 *w;
-  u32 nw, pos;
-  __device__ __forceinline__ u32 peek() const {
-    const u32 i = min(pos >> 5, nw);
-    return __funnelshift_r(w[i], w[i + 1], pos & 31);
+  __device__ __forceinline__ void advance(u32 n) {  // any n
+    if (n <= 32)
+      skip((int)n);
+    else
+      init_at(w, nw, pos + n);
   }
-  __device__ __forceinline__ void skip(int n) { pos += n; }
-  __device__ bool overrun() const { return pos > nw * 32; }
+  __device__ bool overrun() const { return pos > nw * 32u; }
 };
 
 template <class R>
@@ -595,30 +619,16 @@ __device__ __forceinline__ int zeros(R &rd, int lim) {
   return z;
 }
 
-// Parse one block.  FULL: reconstruct it into x; else only move past it.
-// Returns false on a malformed block.
-template <bool LL, bool FULL, class R, class Q = int>
-__device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, unsigned char *sfx,
-                                            Q *qs, int sstride, float (&x)[16]) {
+// The significance section of a nonzero block: per event, the failed group
+// tests of the planes before it, the successful test, the scanned
+// coefficients without the bit and the one found.  Sets bit p of found for
+// every coefficient found and sfx[p * sstride] to the plane it was found at.
+// Returns false on a malformed section.
+template <bool LL, class R>
+__device__ __forceinline__ bool significance(R &rd, int kmin, unsigned char *sfx, int sstride,
+                                             u32 &found) {
   constexpr int Ktop = LL ? 32 : 30;
-  if (!getbits(rd, 1)) {
-    if (FULL) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) x[i] = 0.0f;
-    }
-    return true;
-  }
-  int e = 0, kmin = 0;
-  if (!LL) {
-    const int eb = (int)getbits(rd, 9);
-    if (eb >= kTab) return false;
-    e = eb - 150;
-    kmin = ktab[eb];
-  }
-  // significance section: per event, the failed group tests of the planes
-  // before it, the successful test, the scanned coefficients without the bit
-  // and the one found; sfx[p] keeps the plane of the event at p
-  u32 found = 0;
+  found = 0;
   int n = 0, k = Ktop;
   while (k >= kmin && n < 16) {
     const int lim = k - kmin + 1;
@@ -651,31 +661,147 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
     found |= 1u << p;
     n = p + 1;
   }
-  // refinement: magnitudes and signs, in coding order.  Fixed accuracy takes
-  // a rolled loop (smaller code) through this thread's shared-memory slots
-  // qs[j * sstride], j in block order; lossless keeps the unrolled register
-  // form (its 64-bit slots would cost occupancy).
+  return true;
+}
+
+// The walk of one chunk: the bit offset of each of its first nblk blocks
+// that is not all zero into offs, and its cost class (1 + 16 min(events, 14)
+// + min(members, 15): the trip counts of the decode's two loops) into cls;
+// both arrays come zeroed, and class 0 marks an all-zero block.  Every
+// iteration consumes one token: a run of all-zero blocks, a block's head, or
+// one event of its significance section (failed group tests, the successful
+// one, the scan, the coefficient found).  Every member of the prefix
+// carries w bits and a sign, w the plane above kmin of the next coefficient
+// found, so the refinement section is skipped in one step with the token
+// that ends the significance section.  The lanes of a warp, each on its own
+// chunk, move one token per iteration whatever their blocks look like, and
+// a warp takes as many iterations as its longest chunk has tokens.  Returns
+// false on a malformed chunk.
+template <bool LL>
+__device__ bool walk_chunk(GReader &rd, u32 nblk, const unsigned char *ktab, unsigned short *offs,
+                           unsigned char *cls) {
+  constexpr int Ktop = LL ? 32 : 30;
+  int phase = 0;  // 0 a block's head, 1 an event, 3 a scan past the window
+  int k = 0, kmin = 0, n = 0, g = 0, ne = 0;
+  u32 blk = 0, refine = 0;
+  bool ok = true;
+  while (blk < nblk && ok) {
+    const u32 v = rd.peek();
+    u32 adv = 0;
+    bool event = false;  // an event ends in this token: coefficient n + g at plane k
+    bool done = false;   // the significance section ends with this token
+    if (phase == 0) {
+      if (!(v & 1u)) {  // a run of all-zero blocks (one flag bit each)
+        adv = (u32)min(v ? __ffs(v) - 1 : 32, (int)(nblk - blk));
+        blk += adv;
+      } else {
+        offs[blk] = (unsigned short)rd.pos;  // < 2^16: a chunk holds at most 640 words
+        if (LL) {
+          adv = 1;
+        } else {
+          const int eb = (int)((v >> 1) & 511u);
+          ok = eb < kTab;
+          kmin = ok ? ktab[eb] : 0;
+          adv = 10;
+        }
+        phase = 1;
+        k = Ktop;
+        n = 0;
+        ne = 0;
+        refine = 0;
+      }
+    } else if (phase == 1) {
+      const int lim = k - kmin + 1;
+      const int z = v ? __ffs(v) - 1 : 32;
+      if (z >= lim) {  // every remaining plane fails
+        adv = (u32)lim;
+        done = true;
+      } else if (z == 32) {  // (lossless) 32 failed tests, planes left
+        adv = 32;
+        k -= 32;
+      } else {
+        k -= z;
+        const u32 v2 = z < 31 ? v >> (z + 1) : 0u;  // 31 - z valid bits
+        g = v2 ? __ffs(v2) - 1 : 32;
+        if (g < 31 - z) {
+          adv = (u32)(z + g + 2);
+          event = true;
+        } else {  // the scan goes on past the window
+          adv = 32;
+          g = 31 - z;
+          phase = 3;
+        }
+        ok = g < 16 - n;
+      }
+    } else {
+      const int zz = v ? __ffs(v) - 1 : 32;
+      g += zz;
+      ok = zz < 32 && g < 16 - n;
+      adv = (u32)(zz + 1);
+      event = true;
+      phase = 1;
+    }
+    if (event && ok) {  // members n .. n + g enter the prefix at plane k
+      refine += (u32)(g + 1) * (u32)(k - kmin + 1);
+      n += g + 1;
+      ++ne;
+      done = n == 16;
+    }
+    if (done && ok) {
+      cls[blk] = (unsigned char)(1 + min(ne, 14) * 16 + min(n, 15));
+      adv += refine;
+      phase = 0;
+      ++blk;
+    }
+    rd.advance(adv);
+  }
+  return ok;
+}
+
+// Decode one block into x (the decode).  Returns false on a malformed block.
+template <bool LL, class R>
+__device__ __forceinline__ bool decode_block(R &rd, const unsigned char *ktab,
+                                             unsigned char *sfx, int *qs, int sstride,
+                                             float (&x)[16]) {
+  if (!getbits(rd, 1)) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = 0.0f;
+    return true;
+  }
+  int e = 0, kmin = 0;
+  if (!LL) {
+    const int eb = (int)getbits(rd, 9);
+    if (eb >= kTab) return false;
+    e = eb - 150;
+    kmin = ktab[eb];
+  }
+  u32 found;
+  if (!significance<LL>(rd, kmin, sfx, sstride, found)) return false;
+  // refinement: magnitudes and signs, in coding order, each at the midpoint
+  // of its kept interval.  Fixed accuracy takes a rolled loop over the
+  // members (one trip per member, so lanes with as many members stay in
+  // step), the coefficients through this thread's shared-memory slots qs[j *
+  // sstride], j in block order; lossless keeps the unrolled register form
+  // (its 64-bit slots would cost occupancy).
   using S = typename std::conditional<LL, long long, int>::type;
   S q[16];
   long long qw[16];
+  const u64 half = kmin > 0 ? (1ull << (kmin - 1)) : 0ull;
+  const int n = found ? 32 - __clz(found) : 0;  // members: up to the last coefficient found
   if constexpr (!LL) {
-    if (FULL) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) qs[j * sstride] = 0;
-    }
+    for (int j = 0; j < 16; ++j) qs[j * sstride] = 0;
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
-      const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;  // plane of the next event
-      u64 t = w > 32 ? 0ull : (u64)getbits(rd, min(w, 32));
+      const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;  // 0 .. 30
+      const u32 fs = getbits(rd, w + 1);  // w bits, then the sign
+      u64 t = fs & ((1u << w) - 1u);
       if ((found >> i) & 1u) t |= 1ull << w;
       if (t) {
-        const bool ng = getbits(rd, 1);
-        long long v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
-        if (ng) v = -v;
-        if (FULL) qs[perm_rt(i) * sstride] = (Q)v;
+        const long long v = (long long)((t << kmin) + half);
+        qs[perm_rt(i) * sstride] = (int)((fs >> w) ? -v : v);
       }
     }
-    if (!FULL) return true;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       q[j] = (S)qs[j * sstride];
@@ -689,18 +815,15 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
         const int w = sfx[(i + __ffs(found >> i) - 1) * sstride] - kmin;
         u64 t = w > 32 ? 0ull : (u64)getbits(rd, min(w, 32));
         if ((found >> i) & 1u) t |= 1ull << w;
+        const bool ng = getbits(rd, 1);
         if (t) {
-          const bool ng = getbits(rd, 1);
-          v = (long long)((t << kmin) + (kmin > 0 ? (1ull << (kmin - 1)) : 0ull));
+          v = (long long)((t << kmin) + half);
           if (ng) v = -v;
         }
       }
-      if (FULL) {
-        q[perm(i)] = (S)v;
-        qw[perm(i)] = v;
-      }
+      q[perm(i)] = (S)v;
+      qw[perm(i)] = v;
     }
-    if (!FULL) return true;
   }
   const bool wide = !LL && kmin > 26;  // fixed accuracy with kmin > 26 reconstructs in 64 bits
   bool ok = true;
@@ -760,116 +883,233 @@ __device__ __forceinline__ bool parse_block(R &rd, const unsigned char *ktab, un
   return ok;
 }
 
-template <bool LL>
-__device__ void decode_group(const DecArgs &a, const unsigned char *slot, u32 arr,
-                             const unsigned char *ktab, unsigned short (*offs)[33], u32 *cw, u32 *cstart,
-                             u32 *cnw, unsigned char *sfx, int *qs, bool &bad) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 g = blockIdx.x * kDecWarps + warp;  // this warp's group of 32 chunks
-  const u32 c0 = g * 32;
-  if (c0 >= a.nchunk) return;
-  const u64 nwords = *reinterpret_cast<const u64 *>(slot + 40);
-  const u32 *index = reinterpret_cast<const u32 *>(slot + kHeader);
-  const u32 *words = reinterpret_cast<const u32 *>(slot + kHeader + a.index_bytes);
-  // phase 1: lane l finds the block offsets of chunk c0 + l
-  {
-    const u32 c = c0 + lane;
-    bool ok = true;
-    u32 start = 0, next = 0;
-    if (c < a.nchunk) {
-      start = index[c];
-      next = c + 1 < a.nchunk ? index[c + 1] : (u32)min(nwords, (u64)0xffffffffu);
-      ok = start <= next && next <= nwords && next - start <= (u32)kChunkWords &&
-           (c > 0 || start == 0);
-      if (ok) {
-        GReader rd;
-        rd.init(words, next, start);
-        const u32 b0 = c * kChunk, nblk = min((u32)kChunk, a.nb - b0);
-        float x[16];
-        for (u32 k = 0; k < nblk && ok; ++k) {
-          offs[lane][k] = (unsigned short)(rd.pos - (u64)start * 32);  // < 640 words
-          ok = parse_block<LL, false>(rd, ktab, sfx, qs, kDecWarps * 32, x);
-        }
-        ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next;
-      }
-    }
-    cstart[lane] = start;
-    cnw[lane] = ok ? next - start : 0;
-    if (!ok) bad = true;
-  }
-  __syncwarp();
-  // phase 2: one chunk at a time, one block per lane, coalesced stores
-  float *dst = a.out + (long long)arr * a.n0 * a.n1;
-  for (int j = 0; j < 32; ++j) {
-    const u32 c = c0 + j;
-    if (c >= a.nchunk) break;
-    const u32 nw = cnw[j], st0 = cstart[j];
-    for (u32 i = lane; i < nw + 2; i += 32) cw[i] = i < nw ? __ldg(words + st0 + i) : 0u;
-    __syncwarp();
-    const u32 b = c * kChunk + lane;
-    if (nw && b < a.nb) {
-      SReader rd{cw, nw, offs[j][lane]};
-      float x[16];
-      const bool ok = parse_block<LL, true>(rd, ktab, sfx, qs, kDecWarps * 32, x) && !rd.overrun();
-      if (!ok) bad = true;
-      const u32 bi = b / a.nb1, bj = b - bi * a.nb1;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const long long i = 4ll * bi + r;
-        if (i < a.n0) {
-          float *row = dst + i * a.n1;
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const long long jj = 4ll * bj + cc;
-            if (jj < a.n1) row[jj] = x[4 * r + cc];
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
+
+// The stream header of array arr checked against the call (one thread).
+__device__ __forceinline__ bool header_ok(const DecArgs &a, const unsigned char *slot) {
+  const u32 *h = reinterpret_cast<const u32 *>(slot);
+  const long long *hl = reinterpret_cast<const long long *>(slot + 16);
+  const u64 *hu = reinterpret_cast<const u64 *>(slot + 40);
+  const double tol = *reinterpret_cast<const double *>(slot + 32);
+  const u64 cap = (a.stride - kHeader - a.index_bytes) / 4;
+  return h[0] == kMagic && h[1] == kVersion && h[2] <= 1u && h[3] == (u32)kChunk && hl[0] == a.n0 &&
+         hl[1] == a.n1 && hu[1] == (u64)a.nchunk && hu[0] <= cap &&
+         (h[2] ? tol == 0.0 : (tol > 0.0 && tol < 1e300));
 }
 
-// One kernel per mode (smaller code per kernel); each skips the other mode's
+// The words [start, next) of chunk c, checked against the index and the bit
+// section; false for a malformed index.
+__device__ __forceinline__ bool chunk_words(const DecArgs &a, const unsigned char *slot, u32 c,
+                                            u32 &start, u32 &next) {
+  const u64 nwords = *reinterpret_cast<const u64 *>(slot + 40);
+  const u32 *index = reinterpret_cast<const u32 *>(slot + kHeader);
+  start = index[c];
+  next = c + 1 < a.nchunk ? index[c + 1] : (u32)min(nwords, (u64)0xffffffffu);
+  return start <= next && next <= nwords && next - start <= (u32)kChunkWords &&
+         (c > 0 || start == 0);
+}
+
+__device__ __forceinline__ void report_bad(const DecArgs &a, u32 arr) {
+  atomicExch(a.err, 1);
+  atomicMin(a.err + 1, (int)(a.arr0 + arr));
+}
+
+// Chunk size classes by which a walk CTA orders its chunks: word counts
+// below 48 one by one, then in steps of 16 words.
+__device__ __forceinline__ int walk_key(u32 nw) {
+  return nw < 48u ? (int)nw : min(48 + (int)((nw - 48u) >> 4), kWalkKeys - 1);
+}
+
+// Pass 1 of decoding: the bit offset and the cost class of every block.  One
+// thread per chunk.  The CTA's chunks are first ordered by size class (a
+// counting sort in shared memory), so that a warp walks chunks of similar
+// length: the walk moves one token per iteration and a warp takes as many
+// iterations as its longest chunk.  The offsets and classes go through
+// shared memory to coalesced stores, and the CTA adds its class counts to
+// the call's histogram.  One kernel per mode; each skips the other mode's
 // streams, and the fixed-accuracy one reports bad headers.
 template <bool LL>
-__global__ void __launch_bounds__(kDecWarps * 32) k_cz_decode(const __grid_constant__ DecArgs a) {
-  __shared__ unsigned short s_offs[kDecWarps][32][33];  // block bit offsets in a chunk
-  __shared__ u32 s_cw[kDecWarps][kChunkWords + 2];
-  __shared__ u32 s_start[kDecWarps][32], s_nw[kDecWarps][32];
-  __shared__ unsigned char s_sfx[16][kDecWarps * 32];
-  __shared__ int s_q[LL ? 1 : 16][kDecWarps * 32];  // coefficient slots (fixed accuracy)
+__global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecArgs a) {
+  __shared__ unsigned short s_offs[kWalk][kChunk + 1];
+  __shared__ unsigned char s_cls[kWalk][kChunk + 4];
   __shared__ unsigned char s_kmin[kTab];
+  __shared__ int s_cnt[kClasses];
+  __shared__ unsigned short s_order[kWalk];
+  __shared__ int s_wsum[kWalk / 32];
+  __shared__ u32 s_nnz;
   __shared__ int s_ok;
   const u32 arr = blockIdx.y;
+  const int tid = threadIdx.x;
   const unsigned char *slot = a.in + (u64)arr * a.stride;
-  if (threadIdx.x == 0) {
-    const u32 *h = reinterpret_cast<const u32 *>(slot);
-    const long long *hl = reinterpret_cast<const long long *>(slot + 16);
-    const u64 *hu = reinterpret_cast<const u64 *>(slot + 40);
-    const double tol = *reinterpret_cast<const double *>(slot + 32);
-    const u64 cap = (a.stride - kHeader - a.index_bytes) / 4;
-    s_ok = h[0] == kMagic && h[1] == 2u && h[2] <= 1u && h[3] == (u32)kChunk &&
-           hl[0] == a.n0 && hl[1] == a.n1 && hu[1] == (u64)a.nchunk && hu[0] <= cap &&
-           (h[2] ? tol == 0.0 : (tol > 0.0 && tol < 1e300));
-  }
-  for (int i = threadIdx.x; i < kTab; i += blockDim.x) s_kmin[i] = a.kmin[arr * kTab + i];
+  if (tid == 0) s_ok = header_ok(a, slot);
+  s_cnt[tid] = 0;  // (kClasses == kWalk)
+  for (int i = tid; i < kTab; i += kWalk) s_kmin[i] = a.kmin[arr * kTab + i];
   __syncthreads();
   if (!s_ok) {
-    if (!LL && threadIdx.x == 0 && blockIdx.x == 0) {
-      atomicExch(a.err, 1);
-      atomicMin(a.err + 1, (int)arr);
-    }
+    if (!LL && tid == 0 && blockIdx.x == 0) report_bad(a, arr);
     return;
   }
   if ((reinterpret_cast<const u32 *>(slot)[2] != 0) != LL) return;
-  const int warp = threadIdx.x >> 5;
+  const u32 *words = reinterpret_cast<const u32 *>(slot + kHeader + a.index_bytes);
+  const u32 c0 = blockIdx.x * kWalk;
+  const u32 rows = min((u32)kWalk, a.nchunk - c0);
+  // order the chunks by size class
+  {
+    u32 start = 0, next = 0;
+    const bool ok = (u32)tid < rows && chunk_words(a, slot, c0 + tid, start, next);
+    const int key = walk_key(ok ? next - start : 0u);
+    const int rank = atomicAdd(&s_cnt[key], 1);
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the class counts, two per lane
+      const int x0 = s_cnt[2 * tid], x1 = s_cnt[2 * tid + 1];
+      int inc = x0 + x1;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (tid >= d) inc += y;
+      }
+      const int exc = inc - x0 - x1;
+      s_cnt[2 * tid] = exc;
+      s_cnt[2 * tid + 1] = exc + x0;
+    }
+    __syncthreads();
+    s_order[s_cnt[key] + rank] = (unsigned short)tid;
+    __syncthreads();
+    s_cnt[tid] = 0;  // (now the CTA's class histogram)
+  }
+  const int r = s_order[tid];  // the chunk this thread walks
   bool bad = false;
-  decode_group<LL>(a, slot, arr, s_kmin, s_offs[warp], s_cw[warp], s_start[warp], s_nw[warp],
-                   &s_sfx[0][threadIdx.x], &s_q[0][threadIdx.x], bad);
-  if (bad) {
-    atomicExch(a.err, 1);
-    atomicMin(a.err + 1, (int)arr);
+  if ((u32)r < rows) {
+    const u32 c = c0 + r;
+    u32 start, next;
+    bool ok = chunk_words(a, slot, c, start, next);
+    const u32 nblk = min((u32)kChunk, a.nb - c * kChunk);
+    for (u32 k = 0; k < (u32)kChunk; ++k) {  // (blocks not reached stay all zero)
+      s_offs[r][k] = 0;
+      s_cls[r][k] = 0;
+    }
+    if (ok) {
+      GReader rd;
+      rd.init(words + start, next - start);
+      ok = walk_chunk<LL>(rd, nblk, s_kmin, s_offs[r], s_cls[r]);
+      ok = ok && !rd.overrun() && (rd.pos + 31) / 32 == next - start;
+    }
+    bad = !ok;
+  }
+  __syncthreads();
+  // the segment's list: its blocks that are not all zero, in class order,
+  // each entry the block's index in the segment (13 bits) over its bit
+  // offset in its chunk (15 bits: a chunk holds at most 640 words)
+  const u32 B0 = c0 * kChunk, nblocks = min(rows * kChunk, a.nb - B0);
+  for (u32 i = tid; i < nblocks; i += kWalk) {
+    const unsigned q = s_cls[i >> 5][i & 31];
+    if (q) atomicAdd(&s_cnt[q], 1);
+  }
+  __syncthreads();
+  {  // exclusive scan of the class counts, one per thread
+    const int x = s_cnt[tid], lane = tid & 31, warp = tid >> 5;
+    int inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kWalk / 32; ++w) before += w < warp ? s_wsum[w] : 0;
+    s_cnt[tid] = before + inc - x;
+    if (tid == kWalk - 1) s_nnz = (u32)(before + inc);
+  }
+  __syncthreads();
+  const u64 seg = (u64)arr * a.nseg + blockIdx.x;
+  u32 *list = a.list + seg * kSeg;
+  for (u32 i = tid; i < nblocks; i += kWalk) {
+    const unsigned q = s_cls[i >> 5][i & 31];
+    if (q) list[atomicAdd(&s_cnt[q], 1)] = (i << 15) | s_offs[i >> 5][i & 31];
+  }
+  if (tid == 0) a.segcount[seg] = s_nnz;
+  // the segment's all-zero blocks to the output, row by row: a warp per row,
+  // 32 consecutive floats per store
+  {
+    const u32 B1 = B0 + nblocks, bi0 = B0 / a.nb1, bi1 = (B1 - 1) / a.nb1;
+    const u32 r1 = min(4 * bi1 + 4, (u32)a.n0), lane = tid & 31;
+    for (u32 i = 4 * bi0 + (tid >> 5); i < r1; i += kWalk / 32) {
+      const u32 rb = (i >> 2) * a.nb1;  // first block of this row's block row
+      const u32 lo = max(B0, rb), hi = min(B1, rb + a.nb1);
+      const u32 j1 = min(4 * (hi - rb), (u32)a.n1);
+      float *row = a.out + ((u64)arr * a.n0 + i) * a.n1;
+      for (u32 j = 4 * (lo - rb) + lane; j < j1; j += 32) {
+        const u32 l = rb + (j >> 2) - B0;  // the block's index in the segment
+        if (s_cls[l >> 5][l & 31] == 0) row[j] = 0.0f;
+      }
+    }
+  }
+  if (bad) report_bad(a, arr);
+}
+
+// The 4 x 4 block b of array arr to the output (edge blocks clipped).
+__device__ __forceinline__ void store_block(const DecArgs &a, u32 arr, u32 b, const float (&x)[16]) {
+  const u32 bi = b / a.nb1, bj = b - bi * a.nb1;
+  float *p0 = a.out + ((long long)arr * a.n0 + 4ll * bi) * a.n1 + 4ll * bj;
+  if (4ll * bi + 3 < a.n0 && 4ll * bj + 3 < a.n1) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) p0[cc] = x[4 * r + cc];
+      p0 += a.n1;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (4ll * bi + r < a.n0) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+          if (4ll * bj + cc < a.n1) p0[cc] = x[4 * r + cc];
+      }
+      p0 += a.n1;
+    }
+  }
+}
+
+// Pass 2: decode the listed blocks of one mode, a CTA per segment (a
+// grid-stride loop over one resident wave of CTAs), a thread per entry in
+// list order, so that the lanes of a warp hold blocks of one class and run
+// the decode's loops for as many trips.  Each thread reads its block's bits
+// from global memory, bounded by its chunk.
+template <bool LL>
+__global__ void __launch_bounds__(kDec) k_cz_decode(const __grid_constant__ DecArgs a) {
+  __shared__ unsigned char s_sfx[16][kDec];
+  __shared__ int s_q[LL ? 1 : 16][kDec];  // coefficient slots (fixed accuracy)
+  __shared__ u32 s_n;
+  const int tid = threadIdx.x;
+  const u64 nseg = (u64)a.count * a.nseg;
+  for (u64 seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+    const u32 arr = (u32)(seg / a.nseg), sj = (u32)(seg - (u64)arr * a.nseg);
+    const unsigned char *slot = a.in + (u64)arr * a.stride;
+    if (tid == 0)
+      s_n = header_ok(a, slot) && (reinterpret_cast<const u32 *>(slot)[2] != 0) == LL
+                ? a.segcount[seg]
+                : 0u;
+    __syncthreads();
+    const u32 n = s_n;
+    const u32 *list = a.list + seg * kSeg;
+    const u32 *words = reinterpret_cast<const u32 *>(slot + kHeader + a.index_bytes);
+    for (u32 p = tid; p < n; p += kDec) {
+      const u32 e = list[p];
+      const u32 b = sj * kSeg + (e >> 15);
+      u32 start, next;
+      if (!chunk_words(a, slot, b / kChunk, start, next)) continue;  // (reported by the walk)
+      GReader rd;
+      rd.init_at(words + start, next - start, e & 0x7fffu);
+      float x[16];
+      const bool ok = decode_block<LL>(rd, a.kmin + (u64)arr * kTab, &s_sfx[0][tid],
+                                       &s_q[0][tid], kDec, x) &&
+                      !rd.overrun();
+      if (!ok) report_bad(a, arr);
+      store_block(a, arr, b, x);
+    }
+    __syncthreads();  // (s_n is set again for the next segment)
   }
 }
 
@@ -944,30 +1184,75 @@ cudaError_t launch_cz_encode(const float *data, long long count, long long n0, l
   return cudaGetLastError();
 }
 
-// kmin tables of the streams to decode: count x kTab bytes in tab
+// Arrays decoded per group: at most kGroupBlocks list entries (kSeg per
+// segment), at least one array; the groups of a call are made as even as that
+// allows.
+static long long decode_group(long long count, long long nchunk) {
+  const long long per = (nchunk + kWalk - 1) / kWalk * kSeg;
+  const long long most = std::max(1ll, std::min(count, (long long)(kGroupBlocks / (u64)per)));
+  const long long groups = (count + most - 1) / most;
+  return (count + groups - 1) / groups;
+}
+
+// device scratch of one decompression, in bytes: the 16-byte error record,
+// the kmin tables (count x kTab bytes, padded to 16), then for a group of
+// arrays the segment counts (4 bytes per segment, padded to 16) and lists
+// (4 bytes per block slot)
+u64 codec_decode_scratch_bytes(long long count, long long n0, long long n1) {
+  long long nchunk = 0;
+  if (!codec_shape(n0, n1, nullptr, nullptr, &nchunk, nullptr, nullptr)) return 0;
+  const u64 nseg = (u64)((nchunk + kWalk - 1) / kWalk), G = (u64)decode_group(count, nchunk);
+  return 16 + ((u64)count * kTab + 15) / 16 * 16 + (4 * G * nseg + 15) / 16 * 16 +
+         4ull * kSeg * G * nseg;
+}
+
+// scratch: codec_decode_scratch_bytes(count, n0, n1) bytes, 16-byte aligned;
+// its first 8 bytes must hold {0, 0x7fffffff} (the error record)
 cudaError_t launch_cz_decode(const unsigned char *in, u64 stride, long long count, long long n0,
-                             long long n1, float *out, unsigned char *tab, int *err,
-                             cudaStream_t st) {
+                             long long n1, float *out, unsigned char *scratch, cudaStream_t st) {
   DecArgs a{};
   long long nb1, nb, nchunk;
   if (!codec_shape(n0, n1, &nb1, &nb, &nchunk, &a.index_bytes, nullptr))
     return cudaErrorInvalidValue;
+  if (count < 1 || count > 65535) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 0, per_sm[2] = {0, 0};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_cz_decode<false>, kDec, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_cz_decode<true>, kDec, 0);
+  if (e != cudaSuccess) return e;
   a.nb1 = (u32)nb1;
   a.nb = (u32)nb;
   a.nchunk = (u32)nchunk;
-  a.in = in;
-  a.out = out;
+  a.nseg = (u32)((nchunk + kWalk - 1) / kWalk);
   a.n0 = n0;
   a.n1 = n1;
   a.stride = stride;
-  a.kmin = tab;
-  a.err = err;
-  if (count > 65535) return cudaErrorInvalidValue;
-  const long long groups = (nchunk + 31) / 32;
-  const dim3 grid((unsigned)((groups + kDecWarps - 1) / kDecWarps), (unsigned)count);
+  a.err = reinterpret_cast<int *>(scratch);
+  unsigned char *tab = scratch + 16, *p = tab + ((u64)count * kTab + 15) / 16 * 16;
+  const long long G = decode_group(count, nchunk);
+  a.segcount = reinterpret_cast<u32 *>(p);
+  a.list = reinterpret_cast<u32 *>(p + (4ull * G * a.nseg + 15) / 16 * 16);
   k_cz_kmin<<<(unsigned)count, kTab, 0, st>>>(in, stride, 0.0, tab);
-  k_cz_decode<false><<<grid, kDecWarps * 32, 0, st>>>(a);
-  k_cz_decode<true><<<grid, kDecWarps * 32, 0, st>>>(a);
+  for (long long g0 = 0; g0 < count; g0 += G) {
+    const long long g = std::min(G, count - g0);
+    a.arr0 = (u32)g0;
+    a.count = (u32)g;
+    a.in = in + (u64)g0 * stride;
+    a.out = out + (u64)g0 * (u64)n0 * (u64)n1;
+    a.kmin = tab + (u64)g0 * kTab;
+    const dim3 gwalk(a.nseg, (unsigned)g);
+    // the decode loops over the group's segments with one resident wave of CTAs
+    const u64 nseg = (u64)g * a.nseg;
+    const unsigned gd0 = (unsigned)std::min<u64>(nseg, (u64)std::max(1, per_sm[0]) * nsm);
+    const unsigned gd1 = (unsigned)std::min<u64>(nseg, (u64)std::max(1, per_sm[1]) * nsm);
+    k_cz_walk<false><<<gwalk, kWalk, 0, st>>>(a);
+    k_cz_walk<true><<<gwalk, kWalk, 0, st>>>(a);
+    k_cz_decode<false><<<gd0, kDec, 0, st>>>(a);
+    k_cz_decode<true><<<gd1, kDec, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -1120,13 +1405,12 @@ int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long c
     CZ_CU(dout.alloc(ctx, nbytes_out, st));
     d_data = dout.as<float>();
   }
-  CZ_CU(scratch.alloc(ctx, 16 + (size_t)count * kTab, st));
+  CZ_CU(scratch.alloc(ctx, codec_decode_scratch_bytes(count, n0, n1), st));
   const int init[4] = {0, 0x7fffffff, 0, 0};
   CZ_CU(cudaMemcpyAsync(scratch.p, init, 16, cudaMemcpyHostToDevice, st));
   CodecTimer tm(ctx, st);
   tm.start();
-  CZ_CU(launch_cz_decode(d_in, in_stride, count, n0, n1, d_data,
-                         scratch.as<unsigned char>() + 16, scratch.as<int>(), st));
+  CZ_CU(launch_cz_decode(d_in, in_stride, count, n0, n1, d_data, scratch.as<unsigned char>(), st));
   tm.stop();
   int herr[2] = {0, 0};
   CZ_CU(cudaMemcpyAsync(herr, scratch.p, 8, cudaMemcpyDeviceToHost, st));

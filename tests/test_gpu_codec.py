@@ -182,3 +182,43 @@ def test_migration_through_the_codec(ctx):
     img_err = rel_l2(migrate(sq, round_trip(vel, 1e-4)), ref)
     assert 0 < data_err and img_err <= 10 * data_err, (img_err, data_err)
     print(f"1e-4: seismograms within {data_err:.1e}, image within {img_err:.1e} (relative L2)")
+
+
+def test_damaged_streams_decode_or_are_rejected(ctx):
+    # bytes of valid streams overwritten at seeded positions (header, chunk
+    # index, bit section): every call either decodes or reports the stream
+    # as malformed, and reads stay inside each stream and its chunks, so the
+    # context keeps working
+    x = _arrays(61, 2, 133, 517, "normal")
+    x[1] *= np.exp(-np.arange(133) / 30.0)[:, None].astype(np.float32)
+    count, n0, n1 = x.shape
+    for tol in (1e-3, 0.0):
+        good, stride, sizes = ctx.compress(torch.from_numpy(x).cuda(), tol)
+        ref = torch.zeros(x.shape, dtype=torch.float32, device="cuda")
+        ctx.decompress(good, stride, count, n0, n1, ref)
+        u = inputs.uniform(71 if tol else 73, 4 * 40)
+        nchunk = -(-(-(-n0 // 4) * -(-n1 // 4)) // 32)
+        ib = 16 * -(-nchunk // 4)  # the chunk index follows the 64-byte header
+        rejected = 0
+        for t in range(40):
+            bad = good.clone()
+            s = int(u[4 * t] * count)
+            region = int(u[4 * t + 1] * 3)  # 0 header, 1 index, 2 bit section
+            lo, hi = ((0, 64), (64, 64 + ib), (64 + ib, int(sizes[s])))[region]
+            pos = s * stride + lo + int(u[4 * t + 2] * (hi - lo))
+            bad[pos] ^= 1 + int(u[4 * t + 3] * 255)
+            y = torch.zeros_like(ref)
+            try:
+                ctx.decompress(bad, stride, count, n0, n1, y)
+            except rtm.RTMError as e:
+                assert e.code == rtm.RTM_ERR_ARG
+                assert f"stream {s}" in str(e)
+                rejected += 1
+            else:
+                # accepted: the other stream decodes as before
+                o = 1 - s
+                assert torch.equal(y[o].view(torch.int32), ref[o].view(torch.int32))
+        assert rejected >= 10
+        y = torch.zeros_like(ref)
+        ctx.decompress(good, stride, count, n0, n1, y)
+        assert torch.equal(y.view(torch.int32), ref.view(torch.int32))

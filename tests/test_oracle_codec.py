@@ -110,6 +110,31 @@ def test_hand_coded_lossless_block():
     assert nwords == 2 and index.tolist() == [0] and words.tolist() == [1, 6]
 
 
+def test_hand_coded_block_with_a_scanned_zero_member():
+    # rows [s, s, 0, 0], s the smallest subnormal (ordered integer 1), coded
+    # losslessly.  Each row [1, 1, 0, 0] transforms to (ss, dd, d1, d2) =
+    # (0, -1, 0, 0): d1 = d2 = 0, s1 = 1, s2 = 0, dd = s2 - s1 = -1, ss = s1 +
+    # floor(-1/2) = 0; the columns are then constant, so the one coefficient
+    # left is -1 at (0, 1), coding position 1.  Bits: flag 1 (bit 0); planes
+    # 32..1 fail (bits 1..32); plane 0: group 1 (33), coefficient 0 lacks the
+    # bit (34: 0, a scanned member), coefficient 1 has it (35: 1), group 0
+    # for the other 14 (36); refinement, no planes below 0: the scanned
+    # member's sign bit, 0 as its kept magnitude is zero (37), the found
+    # member's sign, 1 (38).  Word 1 = 2^1 + 2^3 + 2^6 = 74; without a sign
+    # bit for the zero member it would be 42.
+    s = np.uint32(1).view(np.float32)
+    x = np.tile(np.array([s, s, 0.0, 0.0], np.float32), (4, 1))
+    f, _ = oracle.codec_transform(x.view(np.uint32).astype(np.int64))
+    want = np.zeros((4, 4), np.int64)
+    want[0, 1] = -1
+    assert np.array_equal(f, want)
+    blob = oracle.codec_compress(x, 0.0)
+    nwords, index, words = _words(blob)
+    assert nwords == 2 and index.tolist() == [0] and words.tolist() == [1, 74]
+    y = oracle.codec_decompress(blob, 4, 4)
+    assert np.array_equal(y.view(np.uint32), x.view(np.uint32))
+
+
 def test_hand_coded_fixed_accuracy_block():
     # 16 copies of 0.75 at tol 0.5: e = 0 (0.75 = 0.75 2^0), kmin = 22
     # (16 2^22 + 21.5 <= 2^27 < 16 2^23 + 21.5); q = 3 2^26, one coefficient,
