@@ -391,10 +391,9 @@ int rtm_compress(rtm_ctx *ctx, const float *data, long long count, long long n0,
  * data [count][n0][n1] (host or device); count <= 65535.  The mode and the
  * tolerance come from each stream's header.  RTM_ERR_ARG names the first
  * stream that is malformed or was not made for n0 x n1 (the elements of its
- * damaged chunks are then unspecified).  Device scratch of 3 bytes per 4 x 4
- * block (the blocks' bit offsets and decoding cost classes), plus 288 bytes
- * per stream, is taken from
- * the context's pool for the call. */
+ * damaged chunks are then unspecified).  Device scratch of 4 bytes per 4 x 4
+ * block of up to 2^24 blocks at a time (the decode's block lists), plus 288
+ * bytes per stream, is taken from the context's pool for the call. */
 int rtm_decompress(rtm_ctx *ctx, const void *in, uint64_t in_stride, long long count,
                    long long n0, long long n1, float *data, void *stream);
 
