@@ -64,13 +64,14 @@ constexpr int kTile = kChunk * kWarps;   // blocks per encoder tile (one CTA)
 constexpr int kBlockWords = 20;          // 640 bits bound one coded block
 constexpr int kChunkWords = kChunk * kBlockWords;
 constexpr int kTileWords = kTile * kBlockWords;
-constexpr int kWalk = 256;               // decoder's walk: chunks per CTA, one per thread
+constexpr int kWalk = 128;               // decoder's walk: chunks per CTA, one per thread
 constexpr int kWalkKeys = 64;            // size classes the walk orders chunks by
 constexpr int kSeg = kWalk * kChunk;     // blocks of a walk CTA: a segment of the decode's list
 constexpr int kClasses = 256;            // decode cost classes (0: all-zero blocks)
 constexpr int kDec = 256;                // decoder: threads per CTA, one block per thread
 constexpr u64 kGroupBlocks = 1ull << 24; // list entries per group of arrays
-static_assert(kClasses == kWalk, "one class count per walk thread");
+static_assert(kClasses % kWalk == 0 && kWalk % 32 == 0 && kWalk >= 64,
+              "class counts spread evenly over the walk threads");
 static_assert(kSeg <= (1 << 13), "a segment's block index takes 13 bits of a list entry");
 constexpr int kHeader = 64;
 constexpr u32 kMagic = 0x5A4D5452u;
@@ -941,7 +942,7 @@ __global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecAr
   const int tid = threadIdx.x;
   const unsigned char *slot = a.in + (u64)arr * a.stride;
   if (tid == 0) s_ok = header_ok(a, slot);
-  s_cnt[tid] = 0;  // (kClasses == kWalk)
+  for (int i = tid; i < kClasses; i += kWalk) s_cnt[i] = 0;
   for (int i = tid; i < kTab; i += kWalk) s_kmin[i] = a.kmin[arr * kTab + i];
   __syncthreads();
   if (!s_ok) {
@@ -974,7 +975,7 @@ __global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecAr
     __syncthreads();
     s_order[s_cnt[key] + rank] = (unsigned short)tid;
     __syncthreads();
-    s_cnt[tid] = 0;  // (now the CTA's class histogram)
+    for (int i = tid; i < kClasses; i += kWalk) s_cnt[i] = 0;  // (now the class histogram)
   }
   const int r = s_order[tid];  // the chunk this thread walks
   bool bad = false;
@@ -1005,9 +1006,16 @@ __global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecAr
     if (q) atomicAdd(&s_cnt[q], 1);
   }
   __syncthreads();
-  {  // exclusive scan of the class counts, one per thread
-    const int x = s_cnt[tid], lane = tid & 31, warp = tid >> 5;
-    int inc = x;
+  {  // exclusive scan of the class counts, kPerT consecutive ones per thread
+    constexpr int kPerT = kClasses / kWalk;
+    const int lane = tid & 31, warp = tid >> 5;
+    int x[kPerT], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPerT; ++j) {
+      x[j] = s_cnt[tid * kPerT + j];
+      sum += x[j];
+    }
+    int inc = sum;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, inc, d);
@@ -1015,11 +1023,15 @@ __global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecAr
     }
     if (lane == 31) s_wsum[warp] = inc;
     __syncthreads();
-    int before = 0;
+    int run = inc - sum;
 #pragma unroll
-    for (int w = 0; w < kWalk / 32; ++w) before += w < warp ? s_wsum[w] : 0;
-    s_cnt[tid] = before + inc - x;
-    if (tid == kWalk - 1) s_nnz = (u32)(before + inc);
+    for (int w = 0; w < kWalk / 32; ++w) run += w < warp ? s_wsum[w] : 0;
+#pragma unroll
+    for (int j = 0; j < kPerT; ++j) {
+      s_cnt[tid * kPerT + j] = run;
+      run += x[j];
+    }
+    if (tid == kWalk - 1) s_nnz = (u32)run;
   }
   __syncthreads();
   const u64 seg = (u64)arr * a.nseg + blockIdx.x;
