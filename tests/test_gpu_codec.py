@@ -222,3 +222,37 @@ def test_damaged_streams_decode_or_are_rejected(ctx):
         y = torch.zeros_like(ref)
         ctx.decompress(good, stride, count, n0, n1, y)
         assert torch.equal(y.view(torch.int32), ref.view(torch.int32))
+
+
+def test_mixed_modes_over_several_groups(ctx):
+    # 4100 small arrays in one decompression: more blocks than one group of
+    # the decoder's lists holds, so it runs in two groups of 2050; quarters
+    # coded alternately at 1e-3 and losslessly into one buffer, so each
+    # group holds streams of both modes
+    count, n0, n1 = 4100, 20, 23
+    x = _arrays(81, count, n0, n1, "normal")
+    x[::3] *= np.float32(1e-3)  # some arrays with many all-zero blocks at 1e-3
+    d = torch.from_numpy(x).cuda()
+    stride = (rtm.compress_bound(n0, n1) + 15) // 16 * 16
+    out = torch.zeros(count * stride, dtype=torch.uint8, device="cuda")
+    edges = [0, 1025, 2050, 3075, count]
+    tols = np.zeros(count)
+    sizes = []
+    for q in range(4):
+        lo, hi = edges[q], edges[q + 1]
+        tol = 1e-3 if q % 2 == 0 else 0.0
+        tols[lo:hi] = tol
+        _, _, sz = ctx.compress(d[lo:hi].contiguous(), tol, out[lo * stride:hi * stride], stride)
+        sizes += list(sz)
+    y = torch.zeros_like(d)
+    ctx.decompress(out, stride, count, n0, n1, y)
+    got = y.cpu().numpy()
+    blob = out.cpu().numpy()
+    for i in list(range(0, count, 97)) + [1024, 1025, 2049, 2050, 3074, 3075, count - 1]:
+        want = oracle.codec_compress(x[i], tols[i])
+        assert blob[i * stride:i * stride + sizes[i]].tobytes() == want, i
+        ref = oracle.codec_decompress(want, n0, n1)
+        assert np.array_equal(got[i].view(np.uint32), ref.view(np.uint32)), i
+    ll = tols == 0.0
+    assert np.array_equal(got[ll].view(np.uint32), x[ll].view(np.uint32))
+    assert np.abs(got[~ll] - x[~ll]).max() <= 1e-3
