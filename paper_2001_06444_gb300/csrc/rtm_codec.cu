@@ -920,14 +920,16 @@ __device__ __forceinline__ int walk_key(u32 nw) {
   return nw < 48u ? (int)nw : min(48 + (int)((nw - 48u) >> 4), kWalkKeys - 1);
 }
 
-// Pass 1 of decoding: the bit offset and the cost class of every block.  One
-// thread per chunk.  The CTA's chunks are first ordered by size class (a
-// counting sort in shared memory), so that a warp walks chunks of similar
-// length: the walk moves one token per iteration and a warp takes as many
-// iterations as its longest chunk.  The offsets and classes go through
-// shared memory to coalesced stores, and the CTA adds its class counts to
-// the call's histogram.  One kernel per mode; each skips the other mode's
-// streams, and the fixed-accuracy one reports bad headers.
+// Pass 1 of decoding: one thread per chunk, one segment (kWalk chunks) per
+// CTA.  The CTA's chunks are first ordered by size class (a counting sort in
+// shared memory), so that a warp walks chunks of similar length: the walk
+// moves one token per iteration and a warp takes as many iterations as its
+// longest chunk.  The bit offsets and cost classes of the blocks stay in
+// shared memory; the CTA then writes the segment's list (its blocks that are
+// not all zero, ordered by class with a second counting sort) and its count,
+// and writes the all-zero blocks to the output.  One kernel per mode; each
+// skips the other mode's streams, and the fixed-accuracy one reports bad
+// headers.
 template <bool LL>
 __global__ void __launch_bounds__(kWalk) k_cz_walk(const __grid_constant__ DecArgs a) {
   __shared__ unsigned short s_offs[kWalk][kChunk + 1];
