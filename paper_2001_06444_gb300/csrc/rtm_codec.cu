@@ -23,7 +23,7 @@
 // kmin is the largest k >= 1 with 16 2^k + 21.5 <= tol 2^(28-e), else 0.
 //
 // Encoding, in three passes with no device-side waiting:
-//   1. one CTA per tile of 256 blocks (8 chunks), one warp per chunk, one lane
+//   1. one CTA per tile of 128 blocks (4 chunks), one warp per chunk, one lane
 //      per block.  Each lane computes its block's coded length in closed form
 //      (the events of the plane scan are the suffix maxima of the
 //      coefficients' top planes), a warp scan places the blocks, the lanes
@@ -59,7 +59,7 @@ using u64 = unsigned long long;
 
 constexpr int kP = 28;
 constexpr int kChunk = 32;               // blocks per chunk = lanes of a warp
-constexpr int kWarps = 8;                // chunks per encoder tile
+constexpr int kWarps = 4;                // chunks per encoder tile
 constexpr int kTile = kChunk * kWarps;   // blocks per encoder tile (one CTA)
 constexpr int kBlockWords = 20;          // 640 bits bound one coded block
 constexpr int kChunkWords = kChunk * kBlockWords;
@@ -385,10 +385,10 @@ struct Block {
   }
 };
 
-// Pass 1: code one tile (256 blocks, 8 chunks) into its staging slot of
+// Pass 1: code one tile (128 blocks, 4 chunks) into its staging slot of
 // kTileWords words and record the words of each chunk.
 template <bool LL>
-__global__ void __launch_bounds__(kTile, LL ? 2 : 3) k_cz_encode(const __grid_constant__ EncArgs a) {
+__global__ void __launch_bounds__(kTile, LL ? 4 : 6) k_cz_encode(const __grid_constant__ EncArgs a) {
   __shared__ u32 sbuf[kWarps][kChunkWords];
   __shared__ u32 s_words[kWarps];
   __shared__ unsigned char s_kmin[kTab];
