@@ -1324,6 +1324,7 @@ int rtm_ctx_destroy(rtm_ctx *ctx) {
     for (auto &p : ctx->pending) cudaEventDestroy(p.ev);
     ctx->pending.clear();
   }
+  for (cudaStream_t s : ctx->free_streams) cudaStreamDestroy(s);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   delete ctx;
@@ -1575,6 +1576,59 @@ int rtm_model(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_ac
 
 // raw: the stacked imaging numerator (no illumination normalisation, no
 // filter), the adjoint of Born modelling.
+// A call given the legacy default stream, whose launch configuration
+// captures phases into graphs, runs on a context-owned stream instead: after
+// the caller's earlier work on the legacy stream, and before its later work
+// (events join the two).  The legacy stream cannot be captured.
+struct CallStream {
+  rtm_ctx *ctx = nullptr;
+  cudaStream_t user = nullptr, st = nullptr;
+  bool own = false;
+  CallStream() = default;
+  CallStream(const CallStream &) = delete;
+  CallStream &operator=(const CallStream &) = delete;
+  ~CallStream() { end(); }
+  void begin(rtm_ctx *c, cudaStream_t u, bool graph) {
+    ctx = c;
+    user = st = u;
+    if (!graph || (u != nullptr && u != cudaStreamLegacy)) return;
+    cudaStream_t s = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(ctx->stream_mu);
+      if (!ctx->free_streams.empty()) {
+        s = ctx->free_streams.back();
+        ctx->free_streams.pop_back();
+      }
+    }
+    if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    if (!join(u, s)) {  // (stay on the caller's stream)
+      park(s);
+      return;
+    }
+    st = s;
+    own = true;
+  }
+  void end() {
+    if (!own) return;
+    own = false;
+    join(st, user);
+    park(st);
+  }
+
+ private:
+  static bool join(cudaStream_t from, cudaStream_t to) {  // `to` waits for `from`'s work so far
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    const bool ok = cudaEventRecord(ev, from) == cudaSuccess && cudaStreamWaitEvent(to, ev, 0) == cudaSuccess;
+    cudaEventDestroy(ev);  // (released once it completes)
+    return ok;
+  }
+  void park(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(ctx->stream_mu);
+    ctx->free_streams.push_back(s);
+  }
+};
+
 static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const float *vels,
                           const rtm_acq *acq, const float *seis, const rtm_opts *opts,
                           float *images, void *stream, bool raw = false) {
@@ -1587,7 +1641,6 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   if (nsample < 1) return fail(ctx, RTM_ERR_ARG, "nsample must be >= 1");
   if (!vels || !seis || !images) return fail(ctx, RTM_ERR_ARG, "NULL array argument");
   if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   const size_t vbytes = (size_t)nsample * grid->nx * grid->nz * 4;
   const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
   rtm_opts op = *opts;
@@ -1601,6 +1654,9 @@ static int migrate_common(rtm_ctx *ctx, const rtm_grid *grid, int nsample, const
   const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
   const long long nitems = (long long)nsample * acq->nshot;
   const RunConfig cfg = config_for(ctx, *grid, op);
+  CallStream cs;  // (declared before the staging buffers: their frees come before the join)
+  cs.begin(ctx, (cudaStream_t)stream, cfg.graph != 0);
+  const cudaStream_t st = cs.st;
   size_t want = plan.shared_bytes + io + (size_t)nitems * plan.item_bytes;
   const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
   if (cap > 0) want = std::min(want, plan.shared_bytes + io + (size_t)cap * plan.item_bytes);

@@ -72,6 +72,10 @@ struct rtm_ctx {
   std::atomic<int> inject_timeouts{0};  // test hook: calls that start with the flag raised
   rtm_stats stats{};        // guarded by mu
   rtm_server *server = nullptr;
+  // streams on which calls given the legacy default stream run (guarded by
+  // stream_mu): the legacy stream cannot be captured into graphs
+  std::vector<cudaStream_t> free_streams;
+  std::mutex stream_mu;
 };
 
 namespace rtm {

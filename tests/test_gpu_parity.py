@@ -301,6 +301,40 @@ def test_host_buffers_match_device_buffers(ctx, flat):
     assert np.array_equal(host_img, gpu_migrate(ctx, s, s.vel, data[None], isnap=2))
 
 
+def test_legacy_stream_calls_are_ordered(flat):
+    # with graphs on, a call given the legacy default stream runs on a
+    # context-owned stream joined to it by events: it sees the work enqueued
+    # on the legacy stream before it (the velocity, written after a busy
+    # wait), and work enqueued after it sees the image
+    s, data = flat
+    g = _graph_context()
+    try:
+        keep = rtm._Keep()
+        acq = rtm.make_acq(keep, s.src_ix, s.src_iz, s.rec_ix, s.rec_iz, f32(s.wavelet))
+        grid = rtm.make_grid(*s.grid_tuple())
+        opts = rtm.Opts(2, 0, 1e-6, 1)
+        seis = dev(data[None])
+        vel_ref = dev(s.vel)
+        ref = torch.zeros((s.nz, s.nx), dtype=torch.float32, device="cuda")
+        created = torch.cuda.Stream()
+        with torch.cuda.stream(created):
+            g.migrate(grid, vel_ref, acq, seis, opts, ref)
+        created.synchronize()
+        legacy = torch.cuda.default_stream()
+        assert legacy.cuda_stream == 0
+        with torch.cuda.stream(legacy):
+            vel = torch.full_like(vel_ref, 1500.0)
+            torch.cuda._sleep(50_000_000)  # a bounded busy wait on the legacy stream
+            vel.copy_(vel_ref)
+            img = torch.zeros_like(ref)
+            g.migrate(grid, vel, acq, seis, opts, img)
+            out = img * 1.0
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    finally:
+        g.close()
+
+
 def test_full_size_sampled_parity(ctx):
     """The 1701 x 351, 5000-step workload in the bench's launch configuration:
     one shot's seismogram on every 17th receiver and its migrated image
