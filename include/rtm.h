@@ -37,10 +37,11 @@
  *     the given stream and the call then synchronises that stream.  Device
  *     buffers are used in place, the call is asynchronous on `stream` (a
  *     cudaStream_t, NULL = the legacy default stream) unless stated otherwise.
- *     A migration given the legacy default stream, whose launch configuration
- *     captures phases into CUDA graphs, runs on a stream the context owns,
- *     after the work already on the legacy stream and before later work there
- *     (events join the two): the legacy stream cannot be captured.
+ *     A migration or Born modelling given the legacy default stream, whose
+ *     launch configuration captures phases into CUDA graphs, runs on a stream
+ *     the context owns, after the work already on the legacy stream and before
+ *     later work there (events join the two): the legacy stream cannot be
+ *     captured.
  *   - Acquisition arrays (source and receiver indices, the wavelet) are small
  *     and are always HOST memory; they are copied during the call.
  *   - The caller owns every pointer it passes.  The library owns its work

@@ -1725,7 +1725,6 @@ int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq
   if (opts->checkpoint)
     return fail(ctx, RTM_ERR_ARG, "Born modelling keeps every snapshot (checkpoint must be 0)");
   if ((rc = set_device(ctx)) || (rc = check_wait_flag(ctx))) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   const size_t vbytes = (size_t)grid->nx * grid->nz * 4;
   const size_t sbytes = (size_t)acq->nshot * grid->nt * acq->nrec * 4;
   const MigrationPlan plan = plan_migration(*grid, *acq, *opts, 1);
@@ -1733,6 +1732,9 @@ int rtm_born(rtm_ctx *ctx, const rtm_grid *grid, const float *vel, const rtm_acq
                     (is_device_ptr(seis) ? 0 : sbytes);
   const size_t need1 = plan.shared_bytes + plan.item_bytes + io;
   const RunConfig cfg = config_for(ctx, *grid, *opts);
+  CallStream cs;  // (declared before the staging buffers: their frees come before the join)
+  cs.begin(ctx, (cudaStream_t)stream, cfg.graph != 0);
+  const cudaStream_t st = cs.st;
   size_t want = plan.shared_bytes + io + (size_t)acq->nshot * plan.item_bytes;
   const int cap = ctx->max_batch > 0 ? ctx->max_batch : cfg.max_items;
   if (cap > 0) want = std::min(want, plan.shared_bytes + io + (size_t)cap * plan.item_bytes);
